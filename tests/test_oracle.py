@@ -1,0 +1,368 @@
+"""Pins for the CPU oracle: each test checks it against something the paper or
+the mathematics fixes (published vectors, closed forms, invariants, brute
+force), not against itself. No GPU needed."""
+import itertools
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2509_14433_gb300 import workloads as WL
+from tests._graphs import check_forest, edge_ids, min_labels
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+M64 = 2**64 - 1
+
+
+# ---- hashing: SplitMix64 finalizer and key schedule -----------------------
+
+def test_key_schedule_matches_published_splitmix64_vectors():
+    for line in open(os.path.join(GOLD, "splitmix64.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        seed, *want = (int(x) for x in line.split())
+        got = O.keys(seed, len(want))
+        assert [int(x) for x in got] == want
+
+
+def test_mix64_is_the_finalizer_of_the_published_stream():
+    # key j = mix(seed + phi*(j+1)): the published outputs pin mix() itself
+    phi = 0x9E3779B97F4A7C15
+    assert O.mix64((1234567 + phi) & M64) == 6457827717110365317
+    assert O.mix64(phi) == 16294208416658607535
+    assert O.mix64(0) == 0  # the finalizer fixes zero
+
+
+def test_params_closed_form():
+    # lg = ceil(log2 V); L = lg + 2, C = 7, D = 2 lg, W = 1 + C D
+    assert O.params(1024) == (12, 7, 20, 141)
+    assert O.params(16384) == (16, 7, 28, 197)
+    assert O.params(32768) == (17, 7, 30, 211)
+    assert O.params(131072) == (19, 7, 34, 239)
+    assert O.params(5) == (5, 7, 6, 43)
+    assert O.params(1000) == (12, 7, 20, 141)
+    assert O.params(1024, 3, 2, 5) == (3, 2, 5, 11)
+
+
+def test_depth_special_cases():
+    D = 20
+    assert O.depth(1, D) == 0
+    assert O.depth(0xFFFF, D) == 0
+    assert O.depth(2, D) == 1
+    assert O.depth(12, D) == 2
+    for k in range(64):
+        assert O.depth(1 << k, D) == min(k, D - 1)
+    assert O.depth(0, D) == D - 1
+    assert O.depth(1 << 63, 34) == 33
+
+
+def test_depth_law_is_geometric():
+    # P(depth = j) = 2^-(j+1): each index lands in one bucket per column and
+    # half of the mass sits in row 0 (Theorem A.2's one-bucket update).
+    n = 1 << 17
+    key = int(O.keys(7, 1)[0])
+    rng = np.random.default_rng(3)
+    idx = rng.integers(1, 2**40, size=n, dtype=np.uint64)
+    d = np.array([O.depth(O.mix64(int(x) ^ key), 20) for x in idx])
+    for j in range(8):
+        p = 2.0 ** -(j + 1)
+        sd = np.sqrt(n * p * (1 - p))
+        assert abs((d == j).sum() - n * p) < 5 * sd, j
+
+
+# ---- sketch updates: linearity and cancellation (App. A.1.1) ---------------
+
+def _nbrs(rng, V, w, k):
+    c = rng.choice(np.setdiff1d(np.arange(V), [w]), size=k, replace=False)
+    return c.astype(np.uint32)
+
+
+def test_linearity_sketch_of_symmetric_difference():
+    # l0(x) + l0(y) = l0(x + y) over F_2 (App. A.1.1): vertex w's sketch of
+    # neighbour sets A, B XORs to its sketch of A xor B.
+    V, seed, w = 300, 11, 17
+    rng = np.random.default_rng(0)
+    for _ in range(5):
+        A = _nbrs(rng, V, w, 40)
+        B = _nbrs(rng, V, w, 60)
+        sa = O.vertex_sketch(V, seed, w, A)
+        sb = O.vertex_sketch(V, seed, w, B)
+        sab = O.vertex_sketch(V, seed, w, np.setxor1d(A, B))
+        assert np.array_equal(sa ^ sb, sab)
+
+
+def test_single_edge_sketch_returns_that_edge_in_every_layer():
+    # a one-edge characteristic vector: the deterministic bucket alone holds
+    # (idx, G(idx)), so the sample is that edge in every layer.
+    V, seed = 37, 5
+    g = O.Graph(V, seed)
+    for u, v in [(3, 30), (30, 3), (0, 36), (35, 36)]:
+        g = O.Graph(V, seed)
+        assert g.update(np.array([[u, v]], np.uint32)) == O.OK
+        idx = min(u, v) * V + max(u, v)
+        ex = g.export()
+        for r in range(g.L):
+            for w in (u, v):
+                res, e = g.sample(ex[r, w], r)
+                assert (res, e) == (O.GOOD, idx)
+                assert ex[r, w, 0, 0] == idx
+                # exactly one bucket per column besides the deterministic one
+                nz = np.nonzero(ex[r, w, 1:, 0])[0]
+                assert sorted(set(nz // g.D)) == list(range(g.C)) and len(nz) == g.C
+            others = [x for x in range(V) if x not in (u, v)]
+            assert not ex[r, others].any()
+
+
+def test_insert_then_delete_is_identity():
+    V = 64
+    g = O.Graph(V, 9)
+    rng = np.random.default_rng(1)
+    e = WL.uniform_pairs(V, 500, rng)
+    assert g.update(e, np.ones(len(e), np.int8)) == O.OK
+    assert g.export().any()
+    assert g.update(e[::-1], -np.ones(len(e), np.int8)) == O.OK
+    assert not g.export().any()
+
+
+def test_sum_over_all_vertices_is_zero():
+    # every edge (u,v) adds idx to f_u and f_v, so the sum over V cancels
+    # (internal edges cancel, App. A.1.1) in every layer and bucket
+    V = 100
+    g = O.Graph(V, 4)
+    rng = np.random.default_rng(2)
+    steps = WL.toggle_stream(V, WL.er_edges(V, 0.2, 5), 3000, 1000, 10, seed=6)
+    for st in steps:
+        if st[0] == "update":
+            assert g.update(st[1], st[2]) == O.OK
+    ex = g.export()
+    assert ex.any()
+    assert not np.bitwise_xor.reduce(ex, axis=1).any()
+
+
+def test_stream_equals_sketch_of_final_edge_set():
+    # linearity over a whole stream: toggles cancel, so the sketch depends
+    # only on the final edge set
+    V = 80
+    steps = WL.toggle_stream(V, WL.er_edges(V, 0.3, 8), 4000, 1000, 5, seed=9)
+    g1 = O.Graph(V, 3)
+    for st in steps:
+        if st[0] == "update":
+            g1.update(st[1], st[2])
+    final = WL.final_edge_set(V, steps).astype(np.int64)
+    g2 = O.Graph(V, 3)
+    g2.update(np.stack([final // V, final % V], 1).astype(np.uint32))
+    assert np.array_equal(g1.export(), g2.export())
+
+
+# ---- sampling: the cut property (§2.1) ------------------------------------
+
+def test_sample_returns_cut_edge_or_fails_and_zero_iff_cut_empty():
+    rng = np.random.default_rng(4)
+    n_good = n_fail = 0
+    for trial in range(6):
+        V = 64
+        E = WL.er_edges(V, [0.02, 0.05, 0.3][trial % 3], 100 + trial)
+        g = O.Graph(V, 1000 + trial)
+        g.update(E)
+        ids = set(edge_ids(V, E).tolist())
+        for _ in range(60):
+            K = rng.choice(V, size=rng.integers(1, V), replace=False)
+            inK = np.zeros(V, bool)
+            inK[K] = True
+            cut = [x for x in ids if inK[x // V] != inK[x % V]]
+            for r in range(g.L):
+                res, e = g.sample(g.sketch_sum(K, r), r)
+                if not cut:
+                    assert res == O.ZERO
+                    continue
+                assert res != O.ZERO
+                if res == O.GOOD:
+                    assert e in ids and inK[e // V] != inK[e % V]
+                    n_good += 1
+                else:
+                    n_fail += 1
+    assert n_good > 0
+    # Theorem A.2: each query succeeds with probability at least 1 - delta
+    assert n_fail <= 0.01 * (n_good + n_fail)
+
+
+def test_sample_scan_order():
+    V, seed, r = 50, 21, 1
+    g = O.Graph(V, seed)
+    key = O.keys(seed, g.L * (g.C + 1))
+    chk = lambda a: O.mix64(a ^ int(key[r * (g.C + 1) + g.C]))
+    lay = np.zeros((g.W, 2), np.uint64)
+    e1, e2, e3 = 1 * V + 2, 3 * V + 4, 5 * V + 6
+    lay[1 + 2 * g.D + 3] = (e1, chk(e1))
+    lay[1 + 1 * g.D + 5] = (e2, chk(e2))
+    lay[0] = (e1 ^ e2 ^ 99, 12345)  # non-zero, not a valid singleton
+    assert g.sample(lay, r) == (O.GOOD, e2)  # column 1 is scanned before 2
+    lay[1 + 1 * g.D + 5] = (e2, chk(e2) ^ 1)  # broken checksum
+    assert g.sample(lay, r) == (O.GOOD, e1)
+    lay[0] = (e3, chk(e3))
+    assert g.sample(lay, r) == (O.GOOD, e3)  # a good deterministic bucket wins
+    lay[0] = (7 * V + 6, chk(7 * V + 6))  # decodes to u > v: not an edge
+    assert g.sample(lay, r) == (O.GOOD, e1)
+    lay[1 + 2 * g.D + 3] = (0, 0)
+    assert g.sample(lay, r) == (O.FAIL, 0)
+    assert g.sample(np.zeros((g.W, 2), np.uint64), r)[0] == O.ZERO
+
+
+# ---- recovery and queries vs brute force (Problems 1 and 2) ----------------
+
+def test_forests_recover_themselves():
+    for line in open(os.path.join(GOLD, "forests.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        Vs, es, ids, labs = (x.split() for x in line.split(";"))
+        V = int(Vs[0])
+        E = np.array([[int(a) for a in t.split("-")] for t in es], np.uint32).reshape(-1, 2)
+        g = O.Graph(V, 77)
+        if len(E):
+            g.update(E)
+        s, f = g.spanning_forest()
+        assert s == O.OK
+        assert f.tolist() == [int(x) for x in ids]
+        assert g.labels().tolist() == [int(x) for x in labs]
+
+
+@pytest.mark.parametrize("V", [2, 3, 4, 5, 6])
+def test_exhaustive_small_graphs_match_bfs(V):
+    pairs = list(itertools.combinations(range(V), 2))
+    bad = 0
+    for mask in range(1 << len(pairs)):
+        E = np.array([pairs[i] for i in range(len(pairs)) if mask >> i & 1], np.uint32).reshape(-1, 2)
+        g = O.Graph(V, 1 + mask)
+        if len(E):
+            g.update(E)
+        s, f = g.spanning_forest()
+        ids = edge_ids(V, E)
+        if s != O.OK or not np.array_equal(g.labels(), min_labels(V, ids)):
+            bad += 1
+            continue
+        check_forest(V, f, ids)
+    assert bad == 0
+
+
+def test_sampled_seven_vertex_graphs_match_bfs():
+    V = 7
+    pairs = list(itertools.combinations(range(V), 2))
+    rng = np.random.default_rng(7)
+    for mask in rng.integers(0, 1 << len(pairs), size=3000):
+        E = np.array([pairs[i] for i in range(len(pairs)) if int(mask) >> i & 1], np.uint32).reshape(-1, 2)
+        g = O.Graph(V, int(mask) + 5)
+        if len(E):
+            g.update(E)
+        s, f = g.spanning_forest()
+        assert s == O.OK
+        ids = edge_ids(V, E)
+        assert np.array_equal(g.labels(), min_labels(V, ids))
+        check_forest(V, f, ids)
+
+
+@pytest.mark.parametrize("V,p", [(16, 0.1), (64, 0.03), (64, 0.5), (256, 0.004), (256, 0.02), (1000, 0.0015)])
+def test_random_streams_match_bfs(V, p):
+    for seed in range(3):
+        steps = WL.toggle_stream(V, WL.er_edges(V, p, seed), 2 * V, V // 2, 64, seed=seed + 50)
+        g = O.Graph(V, seed + 1)
+        for st in steps:
+            if st[0] == "update":
+                assert g.update(st[1], st[2]) == O.OK
+            else:
+                s, ans = g.query(st[1])
+                assert s == O.OK
+        ids = WL.final_edge_set(V, steps)
+        lab = min_labels(V, ids)
+        assert np.array_equal(g.labels(), lab)
+        s, f = g.spanning_forest()
+        check_forest(V, f, ids)
+        st = g.stats()
+        assert st["complete"] and st["false_pos"] == 0
+        pr = WL.uniform_pairs(V, 500, np.random.default_rng(seed), distinct=False)
+        _, ans = g.query(pr)
+        assert np.array_equal(ans, (lab[pr[:, 0]] == lab[pr[:, 1]]).astype(np.uint8))
+
+
+def _kruskal_replay(V, round_log, reverse=False):
+    comp = np.arange(V)
+    acc = []
+    for live, ids in round_log:
+        parent = {}
+
+        def find(x):
+            while parent.get(x, x) != x:
+                x = parent[x]
+            return x
+
+        for x in sorted(ids.tolist(), reverse=reverse):
+            a, b = find(comp[x // V]), find(comp[x % V])
+            if a != b:
+                parent[max(a, b)] = min(a, b)
+                acc.append(x)
+        comp = np.array([find(c) for c in comp])
+    return sorted(acc)
+
+
+def test_round_forest_is_kruskal_of_logged_candidates():
+    # each round adds the minimum spanning forest (weights = edge ids) of the
+    # distinct candidates over the round-start components; the candidate
+    # graphs here contain cycles, so the order of the candidates matters
+    order_matters = 0
+    for V, p, seed in [(200, 0.01, 12), (200, 0.1, 13), (300, 0.05, 14), (120, 0.3, 15)]:
+        E = WL.er_edges(V, p, seed)
+        g = O.Graph(V, seed + 1)
+        g.update(E)
+        s, f = g.spanning_forest()
+        log = g.round_log()
+        assert _kruskal_replay(V, log) == f.tolist()
+        order_matters += _kruskal_replay(V, log, reverse=True) != f.tolist()
+    assert order_matters > 0
+
+
+def test_queries_recover_only_after_updates():
+    V = 40
+    g = O.Graph(V, 2)
+    g.update(np.array([[0, 1], [1, 2]], np.uint32))
+    s, a = g.query(np.array([[0, 2], [0, 3]], np.uint32))
+    assert s == O.OK and a.tolist() == [1, 0]
+    r1 = g.stats()["rounds"]
+    g.query(np.array([[5, 6]], np.uint32))
+    assert g.stats()["rounds"] == r1
+    g.update(np.array([[2, 3]], np.uint32))
+    s, a = g.query(np.array([[0, 3]], np.uint32))
+    assert a.tolist() == [1]
+    g.update(np.array([[1, 2]], np.uint32), np.array([-1], np.int8))
+    s, a = g.query(np.array([[0, 3], [2, 3], [0, 1]], np.uint32))
+    assert a.tolist() == [0, 1, 1]
+
+
+def test_invalid_batch_applies_nothing_and_is_sticky():
+    V = 16
+    g = O.Graph(V, 3)
+    g.update(np.array([[0, 1]], np.uint32))
+    before = g.export()
+    for e, o in [([[2, 3], [4, 4]], [1, 1]), ([[2, 3], [1, 16]], [1, 1]), ([[2, 3]], [0])]:
+        assert g.update(np.array(e, np.uint32), np.array(o, np.int8)) == O.EINVAL
+        assert np.array_equal(g.export(), before)
+    # while the error is pending, later batches are dropped
+    assert g.update(np.array([[5, 6]], np.uint32)) == O.OK
+    assert np.array_equal(g.export(), before)
+    assert g.sync() == O.EINVAL
+    assert g.sync() == O.OK
+    assert g.update(np.array([[5, 6]], np.uint32)) == O.OK
+    assert not np.array_equal(g.export(), before)
+
+
+def test_too_few_rounds_reports_incomplete():
+    # a path needs about log2(V) Boruvka rounds; with 2 layers it cannot
+    # finish and the status says so
+    V = 64
+    E = np.array([[i, i + 1] for i in range(V - 1)], np.uint32)
+    g = O.Graph(V, 1, L=2)
+    g.update(E)
+    s, f = g.spanning_forest()
+    assert s == O.EINCOMPLETE
+    assert not g.stats()["complete"]
+    check_forest_partial = len(f) < V - 1
+    assert check_forest_partial
