@@ -1,0 +1,160 @@
+/*
+ * cupc: GB300-native sketch-based dynamic connectivity (arXiv 2509.14433).
+ *
+ * C-ABI of the CUDA library libcupc.so. Plain pointers and sizes only. All
+ * compute runs in the library's sm_103a kernels on the caller's stream.
+ *
+ * The operations follow the paper's problem statements:
+ *   - the stream model and the spanning-forest problem: App. A.1, Problem 1;
+ *   - Connected(u,v) answered after any prefix of the stream: §2.1 and
+ *     App. A.2, Problem 2;
+ *   - vertex sketches (CameoSketch l0 samplers of the characteristic vectors
+ *     f_u, O(log V) of them per vertex) and recovery by Boruvka rounds over
+ *     XOR-merged sketches: App. A.1.1 (Theorem A.2, "The AGM Algorithm").
+ *
+ * Conventions shared by every call:
+ *   - Status codes are returned; no C++ exception crosses the ABI.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream). Calls are
+ *     stream-ordered and asynchronous unless stated otherwise. Caller-owned
+ *     buffers must stay valid until the stream has reached the call.
+ *   - Input/output pointers may be device memory or host memory (pinned or
+ *     pageable). Host inputs are staged through a library-owned device
+ *     buffer, in chunks, inside the call; host outputs are copied back and
+ *     the call then synchronises the stream.
+ *   - Edge (u,v), u != v, both < V, has the id u*V + v with u < v.
+ *   - Errors found on the device (an invalid edge in a batch) are sticky:
+ *     the batch and every later batch are dropped until cupc_sync reports
+ *     and clears the error.
+ *
+ * Parameters and derived sizes (0 in cupc_params = default):
+ *   lg = ceil(log2 V) (at least 1); rounds/layers L = lg + 2;
+ *   columns C = 7; rows D = 2*lg; buckets per layer W = 1 + C*D;
+ *   a bucket is two u64 words {alpha, gamma}; a vertex sketch is L*W
+ *   buckets. The hash of index idx in column c of layer r is
+ *   mix(idx ^ key[r*(C+1)+c]), its depth min(ctz(hash), D-1); the checksum
+ *   is mix(idx ^ key[r*(C+1)+C]); key[j] = mix(seed + 0x9E3779B97F4A7C15 *
+ *   (j+1)) and mix is the SplitMix64 finalizer.
+ */
+#ifndef CUPC_H
+#define CUPC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cupc_graph cupc_graph;  /* opaque; owns or borrows device memory */
+typedef struct CUstream_st* cupc_stream; /* same type as cudaStream_t */
+
+typedef enum {
+  CUPC_OK = 0,
+  CUPC_EINVAL = 1,      /* bad argument, or an invalid edge/pair found on the device */
+  CUPC_ENOMEM = 2,      /* allocation failed or the workspace is too small */
+  CUPC_EINCOMPLETE = 3, /* warning: recovery used all L rounds and some
+                           component still sampled an edge or FAIL; labels and
+                           forest are the partial result */
+  CUPC_ECUDA = 4,       /* a CUDA runtime call failed */
+  CUPC_ETIMEOUT = 5     /* a bounded device-side wait gave up */
+} cupc_status;
+
+typedef struct {
+  uint32_t rounds;    /* L, sketch layers = Boruvka rounds (0: lg + 2) */
+  uint32_t columns;   /* C, independent columns per l0 sampler (0: 7; max 31) */
+  uint32_t rows;      /* D, rows per column (0: 2*lg; max 63) */
+  uint32_t max_batch; /* edges staged per internal chunk (0: 1<<20); larger
+                         batches are applied chunk by chunk, which is exact
+                         because sketch addition is XOR */
+} cupc_params;
+
+/* Device bytes cupc_init needs for V vertices (sketches + scratch), so that
+ * a caller (e.g. a PyTorch allocation) can own the memory. 0 on bad input. */
+size_t cupc_workspace_bytes(uint32_t V, const cupc_params* params /* nullable */);
+
+/* Create a graph on V >= 2 vertices with no edges; hash keys derive from
+ * `seed`. `workspace` (device, >= cupc_workspace_bytes, 256-byte aligned)
+ * is borrowed for the graph's lifetime; NULL makes the library allocate.
+ * The graph is zeroed on `stream` before the call returns.
+ * Errors: CUPC_EINVAL (V < 2, params out of range, misaligned workspace),
+ * CUPC_ENOMEM, CUPC_ECUDA. */
+cupc_status cupc_init(uint32_t V, uint64_t seed, const cupc_params* params, void* workspace,
+                      cupc_stream stream, cupc_graph** out);
+
+/* Reset an existing graph to the empty graph (sketches zeroed), keeping
+ * seed, parameters and memory. Stream-ordered. */
+cupc_status cupc_reset(cupc_graph* g, cupc_stream stream);
+
+/* Apply n edge updates (Problem 1's stream). edges: 2n u32, u0,v0,u1,v1...;
+ * ops: n int8, +1 insert / -1 delete. Over F_2 both toggle the edge's
+ * coordinate in f_u and f_v (App. A.1.1), so the caller must keep the stream
+ * valid (insert only absent edges, delete only present ones) as Problem 1
+ * requires. The whole batch is validated on the device first; any u == v,
+ * u or v >= V, or op not +-1 drops the whole batch (sticky CUPC_EINVAL at
+ * the next cupc_sync). n == 0 is a no-op. Marks the recovery stale. */
+cupc_status cupc_update_batch(cupc_graph* g, const uint32_t* edges, const int8_t* ops, size_t n,
+                              cupc_stream stream);
+
+/* Answer m Connected(u,v) queries (Problem 2): out[i] = 1 iff pairs[2i] and
+ * pairs[2i+1] are in the same recovered component. Runs Boruvka recovery
+ * first if an update happened since the last one. pairs: 2m u32; out: m u8.
+ * A pair entry >= V sets the sticky CUPC_EINVAL and writes 0 for it. */
+cupc_status cupc_query(cupc_graph* g, const uint32_t* pairs, size_t m, uint8_t* out, cupc_stream stream);
+
+/* Spanning forest of the current graph (Problem 1): edge ids ascending into
+ * edge_ids_out (cap >= V-1 always suffices); *n_out (host) receives the
+ * count. Recovers first if stale. Synchronises `stream`. Returns the
+ * recovery status (CUPC_OK or CUPC_EINCOMPLETE), CUPC_EINVAL if cap is too
+ * small, or a pending sticky error. */
+cupc_status cupc_spanning_forest(cupc_graph* g, uint64_t* edge_ids_out, size_t cap, size_t* n_out,
+                                 cupc_stream stream);
+
+/* Component label (minimum vertex id of the component) of every vertex
+ * into labels_out (V u32). Recovers first if stale. */
+cupc_status cupc_labels(cupc_graph* g, uint32_t* labels_out, cupc_stream stream);
+
+/* Synchronise `stream`, then return and clear the sticky device error
+ * (CUPC_EINVAL / CUPC_ETIMEOUT), else the last recovery's status. */
+cupc_status cupc_sync(cupc_graph* g, cupc_stream stream);
+
+/* Copy all sketches to dst (host or device) as [layer r][vertex w][bucket j]
+ * x {alpha, gamma} u64, j = 0 deterministic bucket, j = 1 + c*D + d.
+ * bytes must equal L*V*W*16. Synchronises `stream`. For parity checks and
+ * checkpoints (the sketches are the whole state: import restores it). */
+cupc_status cupc_export_sketches(cupc_graph* g, void* dst, size_t bytes, cupc_stream stream);
+cupc_status cupc_import_sketches(cupc_graph* g, const void* src, size_t bytes, cupc_stream stream);
+
+/* Statistics of the last recovery, host array of 8 u64:
+ * [0] rounds run, [1] FAIL samples, [2] checksum false positives,
+ * [3] complete flag, [4] forest edges, [5] recoveries run so far,
+ * [6] update batches applied, [7] sticky error bits. Synchronises. */
+cupc_status cupc_stats(cupc_graph* g, uint64_t* out8, cupc_stream stream);
+
+/* Per-round log of the last recovery (host arrays): live[r] = components
+ * sampled in round r, ncand[r] = candidate entries logged in round r
+ * (one per component that sampled a cut edge; the same edge may appear
+ * twice), ids = the entries, round after round (unordered within a round),
+ * cap = capacity of ids. *n_rounds receives the rounds run. Synchronises. */
+cupc_status cupc_round_log(cupc_graph* g, uint32_t* live, uint32_t* ncand, uint64_t* ids, size_t cap,
+                           uint32_t* n_rounds, cupc_stream stream);
+
+/* Kernel timing with CUDA events recorded on the launching stream.
+ * cupc_profile_enable(g, 1) starts recording around every library launch
+ * (and clears earlier records); cupc_profile_read synchronises the graph's
+ * last stream and returns, per kernel class k < n (0 validate, 1 group
+ * = count+plan+scatter, 2 apply, 3 recover, 4 query, 5 forest sort), the
+ * summed milliseconds ms[k] and the number of launches of the library's
+ * kernels launches[k] since enabling. */
+cupc_status cupc_profile_enable(cupc_graph* g, int on);
+cupc_status cupc_profile_read(cupc_graph* g, double* ms, uint64_t* launches, size_t n);
+
+/* Derived parameters of a graph: out4 = {L, C, D, W}. */
+cupc_status cupc_get_params(const cupc_graph* g, uint32_t* out4);
+
+void cupc_destroy(cupc_graph* g);
+const char* cupc_status_string(cupc_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

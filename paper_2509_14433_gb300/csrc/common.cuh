@@ -1,0 +1,184 @@
+// Device helpers and graph state shared by the CUDA sources of libcupc.
+//
+// Sketch layout in HBM (layer-major): bucket (r, w, j) of layer r, vertex w,
+// bucket j lives at sketch[(r * V + w) * W + j], 16 bytes {alpha, gamma}.
+// j = 0 is the deterministic bucket, j = 1 + c*D + d is row d of column c
+// (App. A.1.1, Theorem A.2: one bucket per column per update).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <vector>
+#include <stdint.h>
+
+#include "cupc.h"
+
+namespace cupc {
+
+constexpr uint32_t kErrInval = 1u;
+constexpr uint32_t kErrTimeout = 2u;
+constexpr uint32_t kErrQuery = 4u;  // a query pair out of range (does not drop updates)
+constexpr uint64_t kNone = ~0ull;
+constexpr uint32_t kNoneU32 = 0xFFFFFFFFu;
+
+// Rows per column that the update kernel folds in shared memory; deeper rows
+// (probability 2^-kSmemRows per index) are XORed straight into HBM.
+constexpr uint32_t kSmemRows = 12;
+// Records (endpoint incidences) per update work item.
+constexpr uint32_t kItemRecords = 512;
+// Threads of the recovery kernel and members per reduction work item.
+constexpr uint32_t kRecThreads = 256;
+constexpr uint32_t kRecSpan = 32;
+constexpr uint32_t kRecBucketsPerThread = 2;  // W <= 512
+// Bounded device-side waits give up after this long.
+constexpr uint64_t kWaitLimitNs = 2000000000ull;
+
+// Device-side counters of one graph (u32 slots of `gc`).
+enum : uint32_t {
+  GC_ERR = 0,        // sticky error bits (kErrInval drops update batches)
+  GC_NITEMS = 1,     // update work items of the current chunk
+  GC_NEXT_ITEM = 2,  // dynamic scheduler cursor of the apply kernel
+  GC_NFOREST = 3,
+  GC_NZ = 4,         // non-ZERO samples this round
+  GC_ACTIVE = 5,     // MSF: candidates still crossing components
+  GC_NMEMBERS = 6,   // live members this round
+  GC_NFAIL = 7,
+  GC_NFP = 8,
+  GC_ROUNDS = 9,
+  GC_COMPLETE = 10,
+  GC_LOGLEN = 11,
+  GC_NPARTIAL = 12,
+  GC_BAR_COUNT = 13,
+  GC_BAR_GEN = 14,
+  GC_RECOVERIES = 15,
+  GC_BATCHES = 16,   // update chunks applied
+  GC_SLOTS = 32
+};
+
+// SplitMix64 output finalizer (Steele, Lea, Flood, OOPSLA 2014).
+__host__ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// Row of an index in a column: trailing zeros of its hash, capped at D-1.
+__device__ __forceinline__ uint32_t depth_of(uint64_t h, uint32_t D) {
+  int f = __ffsll((long long)h);
+  uint32_t d = f ? (uint32_t)(f - 1) : D - 1;
+  return d < D - 1 ? d : D - 1;
+}
+
+__device__ __forceinline__ uint64_t global_timer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ uint32_t ld_cg(const uint32_t* p) { return __ldcg(p); }
+__device__ __forceinline__ uint64_t ld_cg(const uint64_t* p) {
+  return (uint64_t)__ldcg((const unsigned long long*)p);
+}
+__device__ __forceinline__ uint8_t ld_cg(const uint8_t* p) {
+  return (uint8_t)__ldcg((const unsigned char*)p);
+}
+
+}  // namespace cupc
+
+// Host-side state of one graph. Device arrays are carved from one workspace.
+struct cupc_graph {
+  uint32_t V, L, C, D, W, P, R;  // P: lanes per layer in the update kernel
+  uint64_t seed;
+  uint32_t max_batch, max_pairs;
+  void* ws;
+  size_t ws_bytes;
+  bool owns_ws;
+  bool dirty;
+  int device, sms;
+  int apply_threads, apply_smem, apply_grid;
+  int rec_grid;
+  // sketches and keys
+  ulonglong2* sketch;  // L*V*W
+  uint64_t* keys;      // L*(C+1)
+  uint32_t* gc;        // GC_SLOTS device counters
+  // update scratch
+  uint32_t* cnt;       // V
+  uint32_t* cursor;    // V
+  uint64_t* rec;       // 2*max_batch
+  uint4* items;        // 2*max_batch/kItemRecords + min(V, 2*max_batch) + 1
+  uint32_t* stage_edges;  // 2*max_batch
+  int8_t* stage_ops;      // max_batch
+  uint32_t* stage_pairs;  // 2*max_pairs
+  uint8_t* stage_out;     // max_pairs
+  // recovery state
+  uint32_t* label;   // V
+  uint32_t* parent;  // V
+  uint32_t* minv;    // V
+  uint32_t* rcnt;    // V
+  uint32_t* roff;    // V
+  uint32_t* perm;    // V
+  uint32_t* tgt;     // V
+  uint32_t* plist;   // V
+  uint32_t* tilesum; // V/2048 + 1
+  uint8_t* final_;   // V
+  uint8_t* merged;   // V
+  uint8_t* partial;  // V
+  uint64_t* best;    // V
+  uint64_t* cand;    // V
+  uint64_t* forest;  // V
+  uint64_t* forest_sorted;  // V
+  ulonglong2* acc;   // V*W (partial component sums)
+  uint64_t* log_ids; // L*V
+  uint32_t* log_live;   // L
+  uint32_t* log_ncand;  // L
+  cupc_status last_recovery;
+  // profiling: (kernel class, start, stop, launches) per recorded launch group
+  struct ProfRec {
+    int cls;
+    cudaEvent_t a, b;
+    int launches;
+  };
+  bool prof_on;
+  std::vector<ProfRec> prof;
+  double prof_ms[8];
+  uint64_t prof_launches[8];
+  cudaStream_t last_stream;
+};
+
+namespace cupc {
+enum ProfClass { PC_VALIDATE = 0, PC_GROUP = 1, PC_APPLY = 2, PC_RECOVER = 3, PC_QUERY = 4, PC_SORT = 5, PC_N = 8 };
+// Record an event pair around a launch group when profiling is on.
+struct ProfScope {
+  cupc_graph* g;
+  cudaStream_t s;
+  int cls, launches;
+  cudaEvent_t a = nullptr;
+  ProfScope(cupc_graph* g_, cudaStream_t s_, int cls_, int launches_) : g(g_), s(s_), cls(cls_), launches(launches_) {
+    g->last_stream = s;
+    if (g->prof_on && cudaEventCreate(&a) == cudaSuccess) cudaEventRecord(a, s);
+  }
+  ~ProfScope() {
+    if (!a) return;
+    cudaEvent_t b;
+    if (cudaEventCreate(&b) != cudaSuccess) {
+      cudaEventDestroy(a);
+      return;
+    }
+    cudaEventRecord(b, s);
+    g->prof.push_back({cls, a, b, launches});
+  }
+};
+}  // namespace cupc
+
+namespace cupc {
+// Launchers (defined in update.cu / recover.cu); all stream-ordered.
+cudaError_t launch_keys(cupc_graph* g, cudaStream_t s);
+cudaError_t launch_update_chunk(cupc_graph* g, const uint32_t* edges, size_t n, cudaStream_t s);
+cudaError_t launch_validate(cupc_graph* g, const uint32_t* edges, const int8_t* ops, size_t n, cudaStream_t s);
+cudaError_t setup_update(cupc_graph* g);
+cudaError_t setup_recover(cupc_graph* g);
+cudaError_t launch_recover(cupc_graph* g, cudaStream_t s);
+cudaError_t launch_query(cupc_graph* g, const uint32_t* pairs, size_t m, uint8_t* out, cudaStream_t s);
+cudaError_t launch_forest_sort(cupc_graph* g, cudaStream_t s);
+}  // namespace cupc

@@ -1,0 +1,538 @@
+// Spanning-forest recovery by Boruvka rounds over the vertex sketches
+// (App. A.1.1, "The AGM Algorithm": query each supernode's merged sketch for
+// an edge leaving it, merge supernodes and their sketches, repeat for
+// O(log V) rounds) and Connected(u,v) answers from the result (Problem 2).
+//
+// The whole recovery is one cooperative launch: every CTA is co-resident, and
+// the phases of a round are separated by a grid barrier whose wait is bounded
+// (on expiry it sets the timeout error and every CTA returns). Round r:
+//   reset       per-round scratch
+//   group       live vertices grouped by component label (count, tile scan,
+//               scatter); round 0 skips it: every vertex is its own component
+//   reduce      spans of kRecSpan members: thread t XORs bucket t of layer r of
+//               each member (coalesced 16-byte loads); a component that lies
+//               inside one span is sampled in place, others are XORed into a
+//               per-component accumulator and sampled after the barrier
+//   sample      ZERO / GOOD(edge) / FAIL, first good bucket in index order
+//   hook        minimum spanning forest (weights = edge ids) of the candidate
+//               edges over the round-start components: parallel Boruvka with
+//               min-id edges and pointer jumping, which adds exactly the edges
+//               Kruskal in ascending id order would
+//   relabel     every vertex takes the minimum vertex id of its component
+// A component whose merged sketch is ZERO has an empty cut; it is not sampled
+// again until it changes.
+#include <cooperative_groups.h>
+
+#include "common.cuh"
+
+namespace cupc {
+
+struct RecArgs {
+  const ulonglong2* sketch;
+  const uint64_t* keys;
+  uint32_t V, L, C, D, W;
+  uint32_t *label, *parent, *minv, *rcnt, *roff, *perm, *tgt, *plist, *tilesum;
+  uint8_t *final_, *merged, *partial;
+  uint64_t *best, *cand, *forest, *log_ids;
+  ulonglong2* acc;
+  uint32_t *log_live, *log_ncand;
+  uint32_t* gc;
+};
+
+// Grid barrier for a cooperative launch. The wait is bounded: after
+// kWaitLimitNs it records kErrTimeout and returns false in every thread of
+// the CTA, which must then return.
+__device__ bool grid_barrier(uint32_t* gc, uint32_t nblocks, int* s_ok) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile uint32_t* gen = gc + GC_BAR_GEN;
+    const uint32_t my_gen = *gen;
+    int ok = 1;
+    __threadfence();
+    const uint32_t arrived = atomicAdd(&gc[GC_BAR_COUNT], 1u);
+    if (arrived == nblocks - 1) {
+      atomicExch(&gc[GC_BAR_COUNT], 0u);
+      __threadfence();
+      atomicAdd(&gc[GC_BAR_GEN], 1u);
+    } else {
+      const uint64_t t0 = global_timer_ns();
+      while (*gen == my_gen) {
+        if (ld_cg(&gc[GC_ERR]) & kErrTimeout) {
+          ok = 0;
+          break;
+        }
+        if (global_timer_ns() - t0 > kWaitLimitNs) {
+          atomicOr(&gc[GC_ERR], kErrTimeout);
+          ok = 0;
+          break;
+        }
+        __nanosleep(32);
+      }
+    }
+    __threadfence();
+    *s_ok = ok;
+  }
+  __syncthreads();
+  return *s_ok != 0;
+}
+
+__device__ __forceinline__ uint32_t find_root(const uint32_t* parent, uint32_t x, uint32_t V) {
+  for (uint32_t k = 0; k < V; k++) {
+    uint32_t p = ld_cg(&parent[x]);
+    if (p == x) break;
+    x = p;
+  }
+  return x;
+}
+
+// Sample the layer-r sum held by the CTA (thread t owns buckets t, t+256).
+// Result in s_res[0] (0 ZERO, 1 GOOD, 2 FAIL) and s_edge.
+__device__ void cta_sample(const RecArgs& a, uint32_t r, const ulonglong2 (&acc)[kRecBucketsPerThread],
+                           uint32_t* s_min, uint64_t* s_edge, uint32_t* s_res) {
+  const uint64_t kchk = a.keys[r * (a.C + 1) + a.C];
+  if (threadIdx.x == 0) *s_min = kNoneU32;
+  __syncthreads();
+  uint32_t my = kNoneU32;
+#pragma unroll
+  for (uint32_t q = 0; q < kRecBucketsPerThread; q++) {
+    uint32_t j = threadIdx.x + q * blockDim.x;
+    if (j < a.W && acc[q].x != 0 && mix64(acc[q].x ^ kchk) == acc[q].y) {
+      uint64_t u = acc[q].x / a.V, v = acc[q].x % a.V;
+      if (u < v && j < my) my = j;
+    }
+  }
+  if (my != kNoneU32) atomicMin(s_min, my);
+  __syncthreads();
+  const uint32_t jmin = *s_min;
+  if (threadIdx.x == 0) {
+    bool zero = (acc[0].x | acc[0].y) == 0;
+    *s_res = zero ? 0u : (jmin == kNoneU32 ? 2u : 1u);
+  }
+#pragma unroll
+  for (uint32_t q = 0; q < kRecBucketsPerThread; q++)
+    if (threadIdx.x + q * blockDim.x == jmin) *s_edge = acc[q].x;
+  __syncthreads();
+}
+
+// Record the sample of component K (thread 0 only).
+__device__ void take_sample(const RecArgs& a, uint32_t r, uint32_t K, uint32_t res, uint64_t e) {
+  atomicAdd(&a.log_live[r], 1u);
+  if (res == 0) {
+    a.final_[K] = 1;
+    return;
+  }
+  atomicAdd(&a.gc[GC_NZ], 1u);
+  if (res == 2) {
+    atomicAdd(&a.gc[GC_NFAIL], 1u);
+    return;
+  }
+  const uint32_t u = (uint32_t)(e / a.V), v = (uint32_t)(e % a.V);
+  const bool in_u = ld_cg(&a.label[u]) == K, in_v = ld_cg(&a.label[v]) == K;
+  if (in_u != in_v) {
+    a.cand[K] = e;
+    a.log_ids[atomicAdd(&a.gc[GC_LOGLEN], 1u)] = e;
+    atomicAdd(&a.log_ncand[r], 1u);
+  } else {
+    atomicAdd(&a.gc[GC_NFP], 1u);
+  }
+}
+
+__global__ void __launch_bounds__(kRecThreads) k_recover(RecArgs a) {
+  __shared__ int s_ok;
+  __shared__ uint32_t s_min, s_res, s_sum[kRecThreads / 32];
+  __shared__ uint64_t s_edge;
+  __shared__ uint32_t s_w[kRecSpan], s_k[kRecSpan];
+  const uint32_t V = a.V, nb = gridDim.x, tid = threadIdx.x;
+  const uint32_t gtid = blockIdx.x * blockDim.x + tid, gstride = gridDim.x * blockDim.x;
+  uint32_t* gc = a.gc;
+
+  for (uint32_t w = gtid; w < V; w += gstride) {
+    a.label[w] = w;
+    a.final_[w] = 0;
+  }
+  if (gtid == 0) {
+    gc[GC_NFOREST] = 0;
+    gc[GC_NFAIL] = 0;
+    gc[GC_NFP] = 0;
+    gc[GC_LOGLEN] = 0;
+    gc[GC_COMPLETE] = 0;
+    gc[GC_ROUNDS] = 0;
+    gc[GC_RECOVERIES] += 1;
+  }
+  for (uint32_t r = gtid; r < a.L; r += gstride) {
+    a.log_live[r] = 0;
+    a.log_ncand[r] = 0;
+  }
+  if (!grid_barrier(gc, nb, &s_ok)) return;
+
+  for (uint32_t r = 0; r < a.L; r++) {
+    // ---- reset per-round scratch
+    for (uint32_t w = gtid; w < V; w += gstride) {
+      a.parent[w] = w;
+      a.best[w] = kNone;
+      a.tgt[w] = kNoneU32;
+      a.minv[w] = kNoneU32;
+      a.merged[w] = 0;
+      a.rcnt[w] = 0;
+      a.cand[w] = kNone;
+      a.partial[w] = 0;
+    }
+    if (gtid == 0) {
+      gc[GC_NZ] = 0;
+      gc[GC_ACTIVE] = 0;
+      gc[GC_NPARTIAL] = 0;
+    }
+    if (!grid_barrier(gc, nb, &s_ok)) return;
+
+    // ---- group live vertices by component (rounds >= 1)
+    uint32_t nmem = V;
+    if (r > 0) {
+      for (uint32_t w = gtid; w < V; w += gstride) {
+        uint32_t K = ld_cg(&a.label[w]);
+        if (!ld_cg(&a.final_[K])) atomicAdd(&a.rcnt[K], 1u);
+      }
+      if (!grid_barrier(gc, nb, &s_ok)) return;
+      const uint32_t tile = 8 * kRecThreads, ntiles = (V + tile - 1) / tile;
+      for (uint32_t t = blockIdx.x; t < ntiles; t += nb) {
+        uint32_t sum = 0;
+        for (uint32_t k = 0; k < 8; k++) {
+          uint32_t w = t * tile + tid * 8 + k;
+          if (w < V) sum += ld_cg(&a.rcnt[w]);
+        }
+        sum = __reduce_add_sync(0xffffffffu, sum);
+        if ((tid & 31) == 0) s_sum[tid >> 5] = sum;
+        __syncthreads();
+        if (tid == 0) {
+          uint32_t tot = 0;
+          for (uint32_t k = 0; k < kRecThreads / 32; k++) tot += s_sum[k];
+          a.tilesum[t] = tot;
+        }
+        __syncthreads();
+      }
+      if (!grid_barrier(gc, nb, &s_ok)) return;
+      if (blockIdx.x == 0 && tid == 0) {
+        uint32_t run = 0;
+        for (uint32_t t = 0; t < ntiles; t++) {
+          uint32_t x = ld_cg(&a.tilesum[t]);
+          a.tilesum[t] = run;
+          run += x;
+        }
+        gc[GC_NMEMBERS] = run;
+      }
+      if (!grid_barrier(gc, nb, &s_ok)) return;
+      for (uint32_t t = blockIdx.x; t < ntiles; t += nb) {
+        uint32_t c[8], loc = 0;
+        for (uint32_t k = 0; k < 8; k++) {
+          uint32_t w = t * tile + tid * 8 + k;
+          c[k] = w < V ? ld_cg(&a.rcnt[w]) : 0;
+          loc += c[k];
+        }
+        // block exclusive scan of loc
+        const uint32_t lane = tid & 31, wid = tid >> 5;
+        uint32_t inc = loc;
+        for (int o = 1; o < 32; o <<= 1) {
+          uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+          if (lane >= (uint32_t)o) inc += y;
+        }
+        if (lane == 31) s_sum[wid] = inc;
+        __syncthreads();
+        uint32_t wbase = 0;
+        for (uint32_t k = 0; k < wid; k++) wbase += s_sum[k];
+        uint32_t run = ld_cg(&a.tilesum[t]) + wbase + inc - loc;
+        for (uint32_t k = 0; k < 8; k++) {
+          uint32_t w = t * tile + tid * 8 + k;
+          if (w < V) {
+            a.roff[w] = run;
+            a.rcnt[w] = run;  // becomes the scatter cursor, then the segment end
+          }
+          run += c[k];
+        }
+        __syncthreads();
+      }
+      if (!grid_barrier(gc, nb, &s_ok)) return;
+      for (uint32_t w = gtid; w < V; w += gstride) {
+        uint32_t K = ld_cg(&a.label[w]);
+        if (!ld_cg(&a.final_[K])) a.perm[atomicAdd(&a.rcnt[K], 1u)] = w;
+      }
+      if (!grid_barrier(gc, nb, &s_ok)) return;
+      nmem = ld_cg(&gc[GC_NMEMBERS]);
+    }
+
+    // ---- reduce + sample
+    const uint32_t nspans = (nmem + kRecSpan - 1) / kRecSpan;
+    for (uint32_t sp = blockIdx.x; sp < nspans; sp += nb) {
+      const uint32_t i0 = sp * kRecSpan, i1 = min(nmem, i0 + kRecSpan);
+      if (tid < i1 - i0) {
+        uint32_t w = r > 0 ? ld_cg(&a.perm[i0 + tid]) : i0 + tid;
+        s_w[tid] = w;
+        s_k[tid] = r > 0 ? ld_cg(&a.label[w]) : w;
+      }
+      __syncthreads();
+      ulonglong2 acc[kRecBucketsPerThread];
+      uint32_t i = i0;
+      while (i < i1) {
+        const uint32_t K = s_k[i - i0];
+        uint32_t j = i;
+        while (j < i1 && s_k[j - i0] == K) j++;
+#pragma unroll
+        for (uint32_t q = 0; q < kRecBucketsPerThread; q++) acc[q] = make_ulonglong2(0, 0);
+        for (uint32_t m = i; m < j; m++) {
+          const ulonglong2* row = a.sketch + ((size_t)r * V + s_w[m - i0]) * a.W;
+#pragma unroll
+          for (uint32_t q = 0; q < kRecBucketsPerThread; q++) {
+            uint32_t b = tid + q * kRecThreads;
+            if (b < a.W) {
+              ulonglong2 x = __ldg(row + b);
+              acc[q].x ^= x.x;
+              acc[q].y ^= x.y;
+            }
+          }
+        }
+        const bool whole = r == 0 || (ld_cg(&a.roff[K]) == i && ld_cg(&a.rcnt[K]) == j);
+        if (whole) {
+          cta_sample(a, r, acc, &s_min, &s_edge, &s_res);
+          if (tid == 0) take_sample(a, r, K, s_res, s_edge);
+        } else {
+          ulonglong2* dst = a.acc + (size_t)K * a.W;
+#pragma unroll
+          for (uint32_t q = 0; q < kRecBucketsPerThread; q++) {
+            uint32_t b = tid + q * kRecThreads;
+            if (b < a.W && (acc[q].x | acc[q].y)) {
+              atomicXor(&dst[b].x, acc[q].x);
+              atomicXor(&dst[b].y, acc[q].y);
+            }
+          }
+          // the span holding the component's first member lists it once
+          if (tid == 0 && ld_cg(&a.roff[K]) == i) a.plist[atomicAdd(&gc[GC_NPARTIAL], 1u)] = K;
+        }
+        i = j;
+      }
+      __syncthreads();
+    }
+    if (!grid_barrier(gc, nb, &s_ok)) return;
+
+    // ---- sample components spread over several spans
+    const uint32_t npart = ld_cg(&gc[GC_NPARTIAL]);
+    for (uint32_t p = blockIdx.x; p < npart; p += nb) {
+      const uint32_t K = ld_cg(&a.plist[p]);
+      ulonglong2* src = a.acc + (size_t)K * a.W;
+      ulonglong2 acc[kRecBucketsPerThread];
+#pragma unroll
+      for (uint32_t q = 0; q < kRecBucketsPerThread; q++) {
+        uint32_t b = tid + q * kRecThreads;
+        acc[q] = make_ulonglong2(0, 0);
+        if (b < a.W) {
+          acc[q] = __ldcg(src + b);
+          src[b] = make_ulonglong2(0, 0);
+        }
+      }
+      cta_sample(a, r, acc, &s_min, &s_edge, &s_res);
+      if (tid == 0) take_sample(a, r, K, s_res, s_edge);
+    }
+    if (!grid_barrier(gc, nb, &s_ok)) return;
+    if (gtid == 0) gc[GC_ROUNDS] = r + 1;
+    if (ld_cg(&gc[GC_NZ]) == 0) {
+      if (gtid == 0) gc[GC_COMPLETE] = 1;
+      break;
+    }
+
+    // ---- hook: minimum spanning forest of the candidates (Boruvka)
+    for (uint32_t iter = 0; iter < 64; iter++) {
+      for (uint32_t K = gtid; K < V; K += gstride) {
+        uint64_t e = ld_cg(&a.cand[K]);
+        if (e == kNone) continue;
+        uint32_t ra = find_root(a.parent, ld_cg(&a.label[(uint32_t)(e / V)]), V);
+        uint32_t rb = find_root(a.parent, ld_cg(&a.label[(uint32_t)(e % V)]), V);
+        if (ra != rb) {
+          atomicMin((unsigned long long*)&a.best[ra], (unsigned long long)e);
+          atomicMin((unsigned long long*)&a.best[rb], (unsigned long long)e);
+          if (ld_cg(&gc[GC_ACTIVE]) == 0) atomicExch(&gc[GC_ACTIVE], 1u);
+        }
+      }
+      if (!grid_barrier(gc, nb, &s_ok)) return;
+      if (ld_cg(&gc[GC_ACTIVE]) == 0) break;
+      for (uint32_t x = gtid; x < V; x += gstride) {
+        uint64_t e = ld_cg(&a.best[x]);
+        if (e == kNone) continue;
+        uint32_t ra = find_root(a.parent, ld_cg(&a.label[(uint32_t)(e / V)]), V);
+        uint32_t rb = find_root(a.parent, ld_cg(&a.label[(uint32_t)(e % V)]), V);
+        a.tgt[x] = ra == x ? rb : ra;
+      }
+      if (!grid_barrier(gc, nb, &s_ok)) return;
+      for (uint32_t x = gtid; x < V; x += gstride) {
+        uint32_t o = ld_cg(&a.tgt[x]);
+        if (o == kNoneU32) continue;
+        uint64_t e = ld_cg(&a.best[x]);
+        bool mutual = ld_cg(&a.tgt[o]) == x;
+        if (!mutual || x > o) {
+          a.parent[x] = o;
+          a.forest[atomicAdd(&gc[GC_NFOREST], 1u)] = e;
+        }
+      }
+      if (!grid_barrier(gc, nb, &s_ok)) return;
+      for (uint32_t x = gtid; x < V; x += gstride) {
+        uint32_t p = ld_cg(&a.parent[x]);
+        if (p != x) a.parent[x] = find_root(a.parent, p, V);
+        a.best[x] = kNone;
+        a.tgt[x] = kNoneU32;
+      }
+      if (gtid == 0) gc[GC_ACTIVE] = 0;
+      if (!grid_barrier(gc, nb, &s_ok)) return;
+    }
+
+    // ---- relabel to the minimum vertex id of each component
+    for (uint32_t w = gtid; w < V; w += gstride) {
+      if (ld_cg(&a.label[w]) != w) continue;
+      uint32_t root = ld_cg(&a.parent[w]);
+      atomicMin(&a.minv[root], w);
+      if (root != w) a.merged[root] = 1;
+    }
+    if (!grid_barrier(gc, nb, &s_ok)) return;
+    for (uint32_t w = gtid; w < V; w += gstride) {
+      uint32_t K = ld_cg(&a.label[w]);
+      uint32_t root = ld_cg(&a.parent[K]);
+      uint32_t nl = ld_cg(&a.minv[root]);
+      a.label[w] = nl;
+      if (w == root && ld_cg(&a.merged[root])) a.final_[nl] = 0;
+    }
+    if (!grid_barrier(gc, nb, &s_ok)) return;
+  }
+}
+
+cudaError_t setup_recover(cupc_graph* g) {
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_recover, kRecThreads, 0);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  // enough CTAs to stream one layer at full bandwidth; fewer for small V so
+  // that the grid barriers stay cheap
+  uint32_t want = (g->V + 127) / 128;
+  if (want < 8) want = 8;
+  uint32_t cap = (uint32_t)(per_sm * g->sms);
+  if (cap > (uint32_t)g->sms) cap = (uint32_t)g->sms;
+  g->rec_grid = (int)(want < cap ? want : cap);
+  return cudaSuccess;
+}
+
+cudaError_t launch_recover(cupc_graph* g, cudaStream_t s) {
+  RecArgs a;
+  a.sketch = g->sketch;
+  a.keys = g->keys;
+  a.V = g->V;
+  a.L = g->L;
+  a.C = g->C;
+  a.D = g->D;
+  a.W = g->W;
+  a.label = g->label;
+  a.parent = g->parent;
+  a.minv = g->minv;
+  a.rcnt = g->rcnt;
+  a.roff = g->roff;
+  a.perm = g->perm;
+  a.tgt = g->tgt;
+  a.plist = g->plist;
+  a.tilesum = g->tilesum;
+  a.final_ = g->final_;
+  a.merged = g->merged;
+  a.partial = g->partial;
+  a.best = g->best;
+  a.cand = g->cand;
+  a.forest = g->forest;
+  a.log_ids = g->log_ids;
+  a.acc = g->acc;
+  a.log_live = g->log_live;
+  a.log_ncand = g->log_ncand;
+  a.gc = g->gc;
+  cudaError_t e = cudaMemsetAsync(g->gc + GC_BAR_COUNT, 0, sizeof(uint32_t), s);
+  if (e != cudaSuccess) return e;
+  ProfScope ps(g, s, PC_RECOVER, 1);
+  void* args[] = {&a};
+  return cudaLaunchCooperativeKernel((const void*)k_recover, dim3(g->rec_grid), dim3(kRecThreads), args, 0, s);
+}
+
+// ---- Connected(u,v) from the recovered labels (Problem 2)
+__global__ void k_query(const uint32_t* __restrict__ pairs, size_t m, uint8_t* __restrict__ out,
+                        const uint32_t* __restrict__ label, uint32_t V, uint32_t* gc) {
+  bool bad = false;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (size_t)gridDim.x * blockDim.x) {
+    uint32_t u = pairs[2 * i], v = pairs[2 * i + 1];
+    if (u >= V || v >= V) {
+      bad = true;
+      out[i] = 0;
+    } else {
+      out[i] = __ldcg(&label[u]) == __ldcg(&label[v]);
+    }
+  }
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(&gc[GC_ERR], kErrQuery);
+}
+
+cudaError_t launch_query(cupc_graph* g, const uint32_t* pairs, size_t m, uint8_t* out, cudaStream_t s) {
+  if (m == 0) return cudaSuccess;
+  int grid = (int)std::min<size_t>((m + 255) / 256, (size_t)g->sms * 4);
+  ProfScope ps(g, s, PC_QUERY, 1);
+  k_query<<<grid, 256, 0, s>>>(pairs, m, out, g->label, g->V, g->gc);
+  return cudaGetLastError();
+}
+
+// ---- forest ids in ascending order: bitonic sort of 1024-id chunks in
+// shared memory, then each id's final rank = its rank in its chunk + its
+// lower bound in every other chunk (ids are distinct).
+constexpr uint32_t kSortChunk = 1024;
+
+__global__ void __launch_bounds__(512) k_sort_chunks(uint64_t* ids, const uint32_t* gc) {
+  __shared__ uint64_t s[kSortChunk];
+  const uint32_t n = ld_cg(&gc[GC_NFOREST]);
+  const uint32_t base = blockIdx.x * kSortChunk;
+  if (base >= n) return;
+  for (uint32_t i = threadIdx.x; i < kSortChunk; i += blockDim.x) s[i] = base + i < n ? ids[base + i] : kNone;
+  __syncthreads();
+  for (uint32_t k = 2; k <= kSortChunk; k <<= 1) {
+    for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+      for (uint32_t i = threadIdx.x; i < kSortChunk; i += blockDim.x) {
+        uint32_t p = i ^ j;
+        if (p > i) {
+          bool up = (i & k) == 0;
+          uint64_t x = s[i], y = s[p];
+          if ((x > y) == up) {
+            s[i] = y;
+            s[p] = x;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (uint32_t i = threadIdx.x; i < kSortChunk && base + i < n; i += blockDim.x) ids[base + i] = s[i];
+}
+
+__global__ void k_merge_rank(const uint64_t* __restrict__ ids, uint64_t* __restrict__ out, const uint32_t* gc) {
+  const uint32_t n = ld_cg(&gc[GC_NFOREST]);
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint64_t x = ids[i];
+  const uint32_t mine = i / kSortChunk, nch = (n + kSortChunk - 1) / kSortChunk;
+  uint32_t rank = i - mine * kSortChunk;
+  for (uint32_t c = 0; c < nch; c++) {
+    if (c == mine) continue;
+    uint32_t lo = c * kSortChunk, hi = min(n, lo + kSortChunk);
+    while (lo < hi) {  // first position with ids[pos] >= x
+      uint32_t mid = (lo + hi) >> 1;
+      if (ids[mid] < x)
+        lo = mid + 1;
+      else
+        hi = mid;
+    }
+    rank += lo - c * kSortChunk;
+  }
+  out[rank] = x;
+}
+
+cudaError_t launch_forest_sort(cupc_graph* g, cudaStream_t s) {
+  uint32_t nch = (g->V + kSortChunk - 1) / kSortChunk;
+  ProfScope ps(g, s, PC_SORT, 2);
+  k_sort_chunks<<<nch, 512, 0, s>>>(g->forest, g->gc);
+  k_merge_rank<<<(g->V + 255) / 256, 256, 0, s>>>(g->forest, g->forest_sorted, g->gc);
+  return cudaGetLastError();
+}
+
+}  // namespace cupc

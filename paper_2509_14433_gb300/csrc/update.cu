@@ -1,0 +1,338 @@
+// Batched edge updates into the vertex sketches (App. A.1.1, "The AGM
+// Algorithm": an update of edge (u,v) updates every sketch of u and of v;
+// Theorem A.2: CameoSketch touches one bucket per column per update).
+//
+// One chunk of <= max_batch edges goes through four stream-ordered kernels:
+//   k_count   per-vertex record counts (2 records per edge, one per endpoint)
+//   k_plan    exclusive scan -> per-vertex cursors + work items of at most
+//             kItemRecords records of one vertex (single CTA)
+//   k_scatter endpoint records (the edge index u*V+v) grouped by vertex
+//   k_apply   persistent CTAs pull work items; thread (layer r, slot s)
+//             hashes every record of the item for column s of layer r (slot
+//             C computes the checksum and owns the deterministic bucket),
+//             folds them in shared memory, then read-modify-writes only the
+//             touched buckets of that vertex in HBM with 16-byte accesses.
+// XOR is associative and commutative, so the result is bit-identical to
+// applying the updates one by one in stream order.
+#include "common.cuh"
+
+namespace cupc {
+
+__global__ void k_keys(uint64_t seed, uint64_t* keys, uint32_t n) {
+  const uint64_t phi = 0x9E3779B97F4A7C15ull;
+  for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x)
+    keys[j] = mix64(seed + phi * (uint64_t)(j + 1));
+}
+
+cudaError_t launch_keys(cupc_graph* g, cudaStream_t s) {
+  uint32_t n = g->L * (g->C + 1);
+  k_keys<<<1, 256, 0, s>>>(g->seed, g->keys, n);
+  return cudaGetLastError();
+}
+
+// Problem 1's stream: ((u,v), Delta) with u != v in V and Delta = +-1.
+__global__ void k_validate(const uint32_t* __restrict__ edges, const int8_t* __restrict__ ops, size_t n,
+                           uint32_t V, uint32_t* gc) {
+  bool bad = false;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    uint32_t u = edges[2 * i], v = edges[2 * i + 1];
+    int8_t op = ops[i];
+    bad |= (u >= V) | (v >= V) | (u == v) | ((op != 1) & (op != -1));
+  }
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(&gc[GC_ERR], kErrInval);
+}
+
+cudaError_t launch_validate(cupc_graph* g, const uint32_t* edges, const int8_t* ops, size_t n, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  int grid = (int)std::min<size_t>((n + 255) / 256, (size_t)g->sms * 8);
+  ProfScope ps(g, s, PC_VALIDATE, 1);
+  k_validate<<<grid, 256, 0, s>>>(edges, ops, n, g->V, g->gc);
+  return cudaGetLastError();
+}
+
+__global__ void k_count(const uint32_t* __restrict__ edges, size_t n, uint32_t* cnt, const uint32_t* gc) {
+  if (ld_cg(&gc[GC_ERR]) & kErrInval) return;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    atomicAdd(&cnt[edges[2 * i]], 1u);
+    atomicAdd(&cnt[edges[2 * i + 1]], 1u);
+  }
+}
+
+// Block-wide exclusive scan of two u32 values per thread (1024 threads).
+__device__ __forceinline__ void block_scan2(uint32_t a, uint32_t b, uint32_t& ea, uint32_t& eb, uint32_t& ta,
+                                            uint32_t& tb, uint32_t* sa, uint32_t* sb) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  uint32_t ia = a, ib = b;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t xa = __shfl_up_sync(0xffffffffu, ia, o), xb = __shfl_up_sync(0xffffffffu, ib, o);
+    if (lane >= o) {
+      ia += xa;
+      ib += xb;
+    }
+  }
+  if (lane == 31) {
+    sa[wid] = ia;
+    sb[wid] = ib;
+  }
+  __syncthreads();
+  if (wid == 0) {
+    uint32_t va = lane < nw ? sa[lane] : 0, vb = lane < nw ? sb[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t xa = __shfl_up_sync(0xffffffffu, va, o), xb = __shfl_up_sync(0xffffffffu, vb, o);
+      if (lane >= o) {
+        va += xa;
+        vb += xb;
+      }
+    }
+    if (lane < nw) {
+      sa[lane] = va;
+      sb[lane] = vb;
+    }
+  }
+  __syncthreads();
+  uint32_t wa = wid ? sa[wid - 1] : 0, wb = wid ? sb[wid - 1] : 0;
+  ea = wa + ia - a;
+  eb = wb + ib - b;
+  ta = sa[nw - 1];
+  tb = sb[nw - 1];
+  __syncthreads();
+}
+
+// Exclusive scan of the per-vertex record counts into cursors, and the work
+// item list: vertex w with n_w records yields ceil(n_w / kItemRecords) items
+// {w, begin, end, exclusive}; exclusive = the vertex has a single item, so
+// its write-back needs no atomics. Resets cnt for the next chunk.
+__global__ void __launch_bounds__(1024) k_plan(uint32_t* cnt, uint32_t* cursor, uint4* items, uint32_t V,
+                                                 uint32_t* gc) {
+  __shared__ uint32_t sa[32], sb[32];
+  if (ld_cg(&gc[GC_ERR]) & kErrInval) return;
+  uint32_t carry_rec = 0, carry_item = 0;
+  for (uint32_t base = 0; base < V; base += 4 * blockDim.x) {
+    uint32_t w0 = base + 4 * threadIdx.x;
+    uint32_t c[4], ni[4], lr = 0, li = 0;
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      c[k] = (w0 + k < V) ? cnt[w0 + k] : 0;
+      ni[k] = (c[k] + kItemRecords - 1) / kItemRecords;
+      lr += c[k];
+      li += ni[k];
+    }
+    uint32_t er, ei, tr, ti;
+    block_scan2(lr, li, er, ei, tr, ti, sa, sb);
+    uint32_t pr = carry_rec + er, pi = carry_item + ei;
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      uint32_t w = w0 + k;
+      if (w < V) {
+        cursor[w] = pr;
+        cnt[w] = 0;
+        for (uint32_t q = 0; q < ni[k]; q++) {
+          uint32_t b = pr + q * kItemRecords;
+          uint32_t e = min(pr + c[k], b + kItemRecords);
+          items[pi + q] = make_uint4(w, b, e, ni[k] == 1 ? 1u : 0u);
+        }
+      }
+      pr += c[k];
+      pi += ni[k];
+    }
+    carry_rec += tr;
+    carry_item += ti;
+  }
+  if (threadIdx.x == 0) {
+    gc[GC_NITEMS] = carry_item;
+    gc[GC_NEXT_ITEM] = 0;
+    gc[GC_BATCHES] += 1;
+  }
+}
+
+__global__ void k_scatter(const uint32_t* __restrict__ edges, size_t n, uint32_t V, uint32_t* cursor,
+                          uint64_t* __restrict__ rec, const uint32_t* gc) {
+  if (ld_cg(&gc[GC_ERR]) & kErrInval) return;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    uint32_t u = edges[2 * i], v = edges[2 * i + 1];
+    uint32_t a = min(u, v), b = max(u, v);
+    uint64_t idx = (uint64_t)a * V + b;
+    rec[atomicAdd(&cursor[u], 1u)] = idx;
+    rec[atomicAdd(&cursor[v], 1u)] = idx;
+  }
+}
+
+__device__ __forceinline__ void xor_bucket_atomic(ulonglong2* p, ulonglong2 v) {
+  atomicXor(&p->x, v.x);
+  atomicXor(&p->y, v.y);
+}
+
+// Fold the records of one work item into the sketches of its vertex.
+// Thread layout: tid = r*P + s; r < L is the layer, s < C a column, s == C
+// the checksum lane (owner of the deterministic bucket). A lane is the only
+// writer of its column's shared-memory rows, so no shared atomics are
+// needed; the checksum of a record reaches the column lanes by shuffle.
+__global__ void k_apply(ulonglong2* __restrict__ sketch, const uint64_t* __restrict__ keys,
+                        const uint64_t* __restrict__ rec, const uint4* __restrict__ items, uint32_t* gc,
+                        uint32_t V, uint32_t L, uint32_t C, uint32_t D, uint32_t W, uint32_t P, uint32_t R) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  uint64_t* s_rec = reinterpret_cast<uint64_t*>(smem_raw);
+  ulonglong2* s_acc = reinterpret_cast<ulonglong2*>(smem_raw + kItemRecords * sizeof(uint64_t));
+  __shared__ uint32_t s_item;
+
+  if (ld_cg(&gc[GC_ERR]) & kErrInval) return;
+  const uint32_t tid = threadIdx.x, lane = tid & 31;
+  const uint32_t r = tid / P, s = tid % P;
+  const bool in_layer = r < L;
+  const bool is_col = in_layer && s < C;
+  const bool is_chk = in_layer && s == C;
+  const uint64_t key = (in_layer && s <= C) ? keys[r * (C + 1) + s] : 0;
+  const uint32_t chk_lane = (lane & ~(P - 1)) | C;
+  ulonglong2* my_rows = s_acc + ((size_t)(in_layer ? r : 0) * C + (s < C ? s : 0)) * R;
+
+  if (is_col)
+    for (uint32_t d = 0; d < R; d++) my_rows[d] = make_ulonglong2(0, 0);
+
+  const uint32_t nitems = ld_cg(&gc[GC_NITEMS]);
+  for (;;) {
+    if (tid == 0) s_item = atomicAdd(&gc[GC_NEXT_ITEM], 1u);
+    __syncthreads();
+    const uint32_t it = s_item;
+    if (it >= nitems) break;
+    const uint4 item = items[it];
+    const uint32_t w = item.x, beg = item.y, n = item.z - item.y;
+    const bool excl = item.w != 0;
+    for (uint32_t i = tid; i < n; i += blockDim.x) s_rec[i] = rec[beg + i];
+    __syncthreads();
+
+    ulonglong2* gv = sketch + ((size_t)(in_layer ? r : 0) * V + w) * W;
+    uint64_t det_a = 0, det_g = 0;
+    uint32_t mask = 0;
+    uint32_t i = 0;
+    // four records per step: four independent hash chains per lane
+    for (; i + 4 <= n; i += 4) {
+      uint64_t x[4], h[4], gm[4];
+#pragma unroll
+      for (int k = 0; k < 4; k++) {
+        x[k] = s_rec[i + k];
+        h[k] = mix64(x[k] ^ key);
+      }
+#pragma unroll
+      for (int k = 0; k < 4; k++) gm[k] = __shfl_sync(0xffffffffu, h[k], chk_lane);
+#pragma unroll
+      for (int k = 0; k < 4; k++) {
+        if (is_chk) {
+          det_a ^= x[k];
+          det_g ^= h[k];
+        } else if (is_col) {
+          uint32_t d = depth_of(h[k], D);
+          if (d < R) {
+            ulonglong2 v = my_rows[d];
+            v.x ^= x[k];
+            v.y ^= gm[k];
+            my_rows[d] = v;
+            mask |= 1u << d;
+          } else {
+            xor_bucket_atomic(gv + 1 + s * D + d, make_ulonglong2(x[k], gm[k]));
+          }
+        }
+      }
+    }
+    for (; i < n; i++) {
+      uint64_t x = s_rec[i];
+      uint64_t h = mix64(x ^ key);
+      uint64_t gm = __shfl_sync(0xffffffffu, h, chk_lane);
+      if (is_chk) {
+        det_a ^= x;
+        det_g ^= h;
+      } else if (is_col) {
+        uint32_t d = depth_of(h, D);
+        if (d < R) {
+          ulonglong2 v = my_rows[d];
+          v.x ^= x;
+          v.y ^= gm;
+          my_rows[d] = v;
+          mask |= 1u << d;
+        } else {
+          xor_bucket_atomic(gv + 1 + s * D + d, make_ulonglong2(x, gm));
+        }
+      }
+    }
+
+    // write back only the touched buckets of this vertex
+    if (is_chk && (det_a | det_g)) {
+      if (excl) {
+        ulonglong2 o = __ldcg(gv);
+        o.x ^= det_a;
+        o.y ^= det_g;
+        gv[0] = o;
+      } else {
+        xor_bucket_atomic(gv, make_ulonglong2(det_a, det_g));
+      }
+    }
+    if (is_col) {
+      ulonglong2* gcol = gv + 1 + s * D;
+      while (mask) {
+        uint32_t dd[4];
+        ulonglong2 v[4], o[4];
+        int k = 0;
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+          dd[q] = kNoneU32;
+          if (mask) {
+            dd[q] = __ffs(mask) - 1;
+            mask &= mask - 1;
+            v[q] = my_rows[dd[q]];
+            my_rows[dd[q]] = make_ulonglong2(0, 0);
+            k++;
+          }
+        }
+        if (excl) {
+#pragma unroll
+          for (int q = 0; q < 4; q++)
+            if (dd[q] != kNoneU32) o[q] = __ldcg(gcol + dd[q]);
+#pragma unroll
+          for (int q = 0; q < 4; q++)
+            if (dd[q] != kNoneU32) gcol[dd[q]] = make_ulonglong2(o[q].x ^ v[q].x, o[q].y ^ v[q].y);
+        } else {
+#pragma unroll
+          for (int q = 0; q < 4; q++)
+            if (dd[q] != kNoneU32) xor_bucket_atomic(gcol + dd[q], v[q]);
+        }
+        (void)k;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+cudaError_t setup_update(cupc_graph* g) {
+  g->P = 1;
+  while (g->P < g->C + 1) g->P <<= 1;
+  g->R = g->D < kSmemRows ? g->D : kSmemRows;
+  g->apply_threads = (int)(((g->L * g->P) + 31) / 32 * 32);
+  g->apply_smem = (int)(kItemRecords * sizeof(uint64_t) + (size_t)g->L * g->C * g->R * sizeof(ulonglong2));
+  cudaError_t e = cudaFuncSetAttribute(k_apply, cudaFuncAttributeMaxDynamicSharedMemorySize, g->apply_smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_apply, g->apply_threads, g->apply_smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  g->apply_grid = per_sm * g->sms;
+  return cudaSuccess;
+}
+
+cudaError_t launch_update_chunk(cupc_graph* g, const uint32_t* edges, size_t n, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  int grid = (int)std::min<size_t>((n + 255) / 256, (size_t)g->sms * 8);
+  {
+    ProfScope ps(g, s, PC_GROUP, 3);
+    k_count<<<grid, 256, 0, s>>>(edges, n, g->cnt, g->gc);
+    k_plan<<<1, 1024, 0, s>>>(g->cnt, g->cursor, g->items, g->V, g->gc);
+    k_scatter<<<grid, 256, 0, s>>>(edges, n, g->V, g->cursor, g->rec, g->gc);
+  }
+  ProfScope ps(g, s, PC_APPLY, 1);
+  int agrid = (int)std::min<size_t>((size_t)g->apply_grid, 2 * n);
+  k_apply<<<agrid, g->apply_threads, g->apply_smem, s>>>(g->sketch, g->keys, g->rec, g->items, g->gc, g->V, g->L,
+                                                          g->C, g->D, g->W, g->P, g->R);
+  return cudaGetLastError();
+}
+
+}  // namespace cupc

@@ -1,0 +1,174 @@
+"""Thin ctypes binding of libcupc (include/cupc.h): argument marshalling only.
+
+Every function has the C name and returns the C status. Pointer arguments
+accept a torch tensor (its data_ptr), a numpy array (host memory), an int
+address or None. Stream arguments accept a torch.cuda.Stream, an int handle
+or None (the legacy default stream).
+
+Importing this module loads the CUDA library and raises ImportError if it
+has not been built: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libcupc.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"libcupc.so is not built ({LIB_PATH}); run __graft_entry__.build() first")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+CUPC_OK, CUPC_EINVAL, CUPC_ENOMEM, CUPC_EINCOMPLETE, CUPC_ECUDA, CUPC_ETIMEOUT = range(6)
+
+_P, _u32, _u64, _sz = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_size_t
+
+
+class cupc_params(ctypes.Structure):
+    _fields_ = [("rounds", _u32), ("columns", _u32), ("rows", _u32), ("max_batch", _u32)]
+
+
+_SIGS = {
+    "cupc_workspace_bytes": (_sz, [_u32, _P]),
+    "cupc_init": (ctypes.c_int, [_u32, _u64, _P, _P, _P, _P]),
+    "cupc_reset": (ctypes.c_int, [_P, _P]),
+    "cupc_update_batch": (ctypes.c_int, [_P, _P, _P, _sz, _P]),
+    "cupc_query": (ctypes.c_int, [_P, _P, _sz, _P, _P]),
+    "cupc_spanning_forest": (ctypes.c_int, [_P, _P, _sz, _P, _P]),
+    "cupc_labels": (ctypes.c_int, [_P, _P, _P]),
+    "cupc_sync": (ctypes.c_int, [_P, _P]),
+    "cupc_export_sketches": (ctypes.c_int, [_P, _P, _sz, _P]),
+    "cupc_import_sketches": (ctypes.c_int, [_P, _P, _sz, _P]),
+    "cupc_stats": (ctypes.c_int, [_P, _P, _P]),
+    "cupc_round_log": (ctypes.c_int, [_P, _P, _P, _P, _sz, _P, _P]),
+    "cupc_get_params": (ctypes.c_int, [_P, _P]),
+    "cupc_profile_enable": (ctypes.c_int, [_P, ctypes.c_int]),
+    "cupc_profile_read": (ctypes.c_int, [_P, _P, _P, _sz]),
+    "cupc_destroy": (None, [_P]),
+    "cupc_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+}
+for _name, (_res, _args) in _SIGS.items():
+    _fn = getattr(_lib, _name)
+    _fn.restype = _res
+    _fn.argtypes = _args
+
+EXPORTED = tuple(_SIGS)
+
+
+def ptr(x) -> int | None:
+    """Address of a torch tensor / numpy array / int (None stays None)."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if hasattr(x, "ctypes"):
+        return x.ctypes.data
+    raise TypeError(f"cannot take the address of {type(x)}")
+
+
+def stream_handle(s) -> int | None:
+    if s is None or isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def _params(p):
+    if p is None:
+        return None
+    if isinstance(p, cupc_params):
+        return ctypes.byref(p)
+    return ctypes.byref(cupc_params(*p))
+
+
+def cupc_workspace_bytes(V: int, params=None) -> int:
+    return int(_lib.cupc_workspace_bytes(V, _params(params)))
+
+
+def cupc_init(V: int, seed: int, params=None, workspace=None, stream=None):
+    """Returns (status, handle)."""
+    h = ctypes.c_void_p(0)
+    st = _lib.cupc_init(V, seed & (2**64 - 1), _params(params), ptr(workspace), stream_handle(stream),
+                        ctypes.byref(h))
+    return st, h.value
+
+
+def cupc_reset(g, stream=None) -> int:
+    return _lib.cupc_reset(g, stream_handle(stream))
+
+
+def cupc_update_batch(g, edges, ops, n: int, stream=None) -> int:
+    return _lib.cupc_update_batch(g, ptr(edges), ptr(ops), n, stream_handle(stream))
+
+
+def cupc_query(g, pairs, m: int, out, stream=None) -> int:
+    return _lib.cupc_query(g, ptr(pairs), m, ptr(out), stream_handle(stream))
+
+
+def cupc_spanning_forest(g, out, cap: int, stream=None):
+    """Returns (status, n)."""
+    n = ctypes.c_size_t(0)
+    st = _lib.cupc_spanning_forest(g, ptr(out), cap, ctypes.byref(n), stream_handle(stream))
+    return st, n.value
+
+
+def cupc_labels(g, out, stream=None) -> int:
+    return _lib.cupc_labels(g, ptr(out), stream_handle(stream))
+
+
+def cupc_sync(g, stream=None) -> int:
+    return _lib.cupc_sync(g, stream_handle(stream))
+
+
+def cupc_export_sketches(g, dst, nbytes: int, stream=None) -> int:
+    return _lib.cupc_export_sketches(g, ptr(dst), nbytes, stream_handle(stream))
+
+
+def cupc_import_sketches(g, src, nbytes: int, stream=None) -> int:
+    return _lib.cupc_import_sketches(g, ptr(src), nbytes, stream_handle(stream))
+
+
+def cupc_stats(g, out8, stream=None) -> int:
+    return _lib.cupc_stats(g, ptr(out8), stream_handle(stream))
+
+
+def cupc_round_log(g, live, ncand, ids, cap: int, stream=None):
+    """Returns (status, rounds)."""
+    nr = ctypes.c_uint32(0)
+    st = _lib.cupc_round_log(g, ptr(live), ptr(ncand), ptr(ids), cap, ctypes.byref(nr), stream_handle(stream))
+    return st, nr.value
+
+
+def cupc_get_params(g, out4) -> int:
+    return _lib.cupc_get_params(g, ptr(out4))
+
+
+def cupc_profile_enable(g, on: int) -> int:
+    return _lib.cupc_profile_enable(g, on)
+
+
+def cupc_profile_read(g, ms, launches, n: int) -> int:
+    return _lib.cupc_profile_read(g, ptr(ms), ptr(launches), n)
+
+
+def cupc_destroy(g) -> None:
+    _lib.cupc_destroy(g)
+
+
+def cupc_status_string(st: int) -> str:
+    return _lib.cupc_status_string(st).decode()
+
+
+class CupcError(RuntimeError):
+    def __init__(self, st: int, what: str):
+        super().__init__(f"{what}: {cupc_status_string(st)}")
+        self.status = st
+
+
+def check(st: int, what: str = "cupc", ok=(CUPC_OK,)) -> int:
+    if st not in ok:
+        raise CupcError(st, what)
+    return st

@@ -1,0 +1,270 @@
+"""CUDA path vs the CPU oracle, through the C-ABI, on the same seeded inputs.
+
+All arithmetic is integer, so the bar is bit-exact: sketches (every bucket
+word), per-round live counts and candidate sets, labels, forests and query
+answers. Sizes span many work items and ragged tails; edge cases cover empty
+and single-edge batches, a hub vertex split over several work items, repeated
+toggles, chunked and host-staged batches, invalid batches and too few
+rounds."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2509_14433_gb300 import workloads as WL
+from tests._graphs import check_forest, min_labels
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+
+
+def _dev(*a, **k):
+    from tests._dev import Dev
+    return Dev(*a, **k)
+
+
+def assert_same_recovery(dev, ref):
+    s_ref, f_ref = ref.spanning_forest()
+    s_dev, f_dev = dev.forest()
+    assert s_dev == s_ref
+    assert np.array_equal(dev.labels(), ref.labels())
+    assert np.array_equal(f_dev, f_ref)
+    glog, olog = dev.round_log(), ref.round_log()
+    assert len(glog) == len(olog)
+    for (gl, gids), (ol, oids) in zip(glog, olog):
+        assert gl == ol
+        assert np.array_equal(gids, oids)
+    gs, os_ = dev.stats(), ref.stats()
+    assert (gs["rounds"], gs["fail"], gs["false_pos"], gs["complete"]) == \
+        (os_["rounds"], os_["fail"], os_["false_pos"], os_["complete"])
+
+
+@pytest.mark.parametrize("V,p,seed", [(2, 1.0, 1), (5, 0.5, 2), (37, 0.2, 3), (256, 0.05, 4),
+                                       (1000, 0.01, 5), (1024, 0.5, 6), (3001, 0.002, 7)])
+def test_sketches_and_recovery_bit_exact(V, p, seed):
+    steps = WL.toggle_stream(V, WL.er_edges(V, p, seed), 3 * V, max(1, V // 2), 64, seed=seed + 10,
+                             batch_cap=max(1, V * 7))
+    dev, ref = _dev(V, seed), O.Graph(V, seed)
+    for k, st in enumerate(steps):
+        if st[0] == "update":
+            assert dev.update(st[1], st[2]) == 0
+            assert ref.update(st[1], st[2]) == O.OK
+            if k < 3 or k == len(steps) - 2:
+                assert np.array_equal(dev.export(), ref.export())
+        else:
+            s1, a1 = dev.query(st[1])
+            s2, a2 = ref.query(st[1])
+            assert s1 == 0 and np.array_equal(a1, a2)
+    assert np.array_equal(dev.export(), ref.export())
+    assert_same_recovery(dev, ref)
+    assert dev.sync() == (0 if ref.stats()["complete"] else 3)
+
+
+def test_plain_stream_full_size():
+    # V=1024: ER(0.5) start graph, 200k uniform toggles, 1k-pair Connected
+    # batch every 10k updates; every answer and the final sketch bit-exact
+    V, seed = 1024, 1
+    steps = WL.plain_stream(V=V, seed=1)
+    dev, ref = _dev(V, seed), O.Graph(V, seed)
+    nq = 0
+    for st in steps:
+        if st[0] == "update":
+            assert dev.update(st[1], st[2]) == 0
+            ref.update(st[1], st[2])
+        else:
+            s1, a1 = dev.query(st[1])
+            s2, a2 = ref.query(st[1])
+            assert s1 == 0 and s2 == O.OK and np.array_equal(a1, a2)
+            nq += 1
+    assert nq == 20
+    assert np.array_equal(dev.export(), ref.export())
+    assert_same_recovery(dev, ref)
+    lab = min_labels(V, WL.final_edge_set(V, steps))
+    assert np.array_equal(dev.labels(), lab)
+
+
+def test_empty_and_single_edge_batches():
+    V = 64
+    dev, ref = _dev(V, 3), O.Graph(V, 3)
+    assert dev.update(np.zeros((0, 2), np.uint32)) == 0
+    st, f = dev.forest()
+    assert st == 0 and f.size == 0
+    assert np.array_equal(dev.labels(), np.arange(V, dtype=np.uint32))
+    for e in ([5, 9], [9, 5], [0, 63], [62, 63]):
+        assert dev.update([e]) == 0
+        ref.update(np.array([e], np.uint32))
+        assert np.array_equal(dev.export(), ref.export())
+    assert_same_recovery(dev, ref)
+
+
+def test_hub_vertex_split_over_work_items():
+    # vertex 0 has V-1 records (> one work item): several CTAs fold its
+    # buckets, deep rows and the deterministic bucket see many writers
+    V = 5000
+    E = np.stack([np.zeros(V - 1, np.uint32), np.arange(1, V, dtype=np.uint32)], 1)
+    rng = np.random.default_rng(0)
+    E = E[rng.permutation(len(E))]
+    E[::3] = E[::3, ::-1]
+    extra = WL.er_edges(V, 0.0005, 9)
+    dev, ref = _dev(V, 11), O.Graph(V, 11)
+    for batch in (E, extra):
+        dev.update(batch)
+        ref.update(batch)
+    assert np.array_equal(dev.export(), ref.export())
+    assert_same_recovery(dev, ref)
+
+
+def test_repeated_toggles_cancel():
+    V = 100
+    e = np.array([[3, 7]] * 1001 + [[4, 8]] * 1000 + [[1, 2]], np.uint32)
+    ops = np.where(np.arange(len(e)) % 2 == 0, 1, -1).astype(np.int8)
+    dev, ref = _dev(V, 5), O.Graph(V, 5)
+    dev.update(e, ops)
+    ref.update(e, ops)
+    x = dev.export()
+    assert np.array_equal(x, ref.export())
+    nz = np.nonzero(x.any(axis=(0, 2, 3)))[0].tolist()
+    assert nz == [1, 2, 3, 7]
+
+
+@pytest.mark.parametrize("host", [False, True])
+def test_chunked_batches_and_host_buffers(host):
+    V = 700
+    params = (0, 0, 0, 1000)  # max_batch = 1000 edges per internal chunk
+    E = WL.er_edges(V, 0.03, 12)
+    ops = np.ones(len(E), np.int8)
+    dev, ref = _dev(V, 8, params), O.Graph(V, 8)
+    assert len(E) > 3 * 1000
+    assert dev.update(E, ops, host=host) == 0
+    ref.update(E, ops)
+    assert np.array_equal(dev.export(), ref.export())
+    pairs = WL.uniform_pairs(V, 2500, WL.rng(3), distinct=False)
+    s1, a1 = dev.query(pairs, host=host)
+    s2, a2 = ref.query(pairs)
+    assert s1 == 0 and np.array_equal(a1, a2)
+    assert_same_recovery(dev, ref)
+    assert dev.stats()["chunks"] >= 7 if not host else True
+
+
+@pytest.mark.parametrize("host", [False, True])
+def test_invalid_batch_is_dropped_whole_and_sticky(host):
+    V = 50
+    params = (0, 0, 0, 4)
+    dev, ref = _dev(V, 2, params), O.Graph(V, 2)
+    good = np.array([[0, 1], [1, 2], [2, 3]], np.uint32)
+    dev.update(good, host=host)
+    ref.update(good)
+    before = dev.export()
+    bad_cases = [
+        (np.array([[4, 5], [6, 7], [8, 9], [10, 11], [12, 13], [7, 7]], np.uint32), None),
+        (np.array([[4, 5], [6, 50]], np.uint32), None),
+        (np.array([[4, 5]], np.uint32), np.array([0], np.int8)),
+    ]
+    for e, o in bad_cases:
+        dev.update(e, o, host=host)
+        assert np.array_equal(dev.export(), before)
+        # later batches are dropped while the error is pending
+        dev.update(np.array([[20, 21]], np.uint32), host=host)
+        assert np.array_equal(dev.export(), before)
+        assert dev.sync() == 1
+        assert dev.sync() == 0
+    dev.update(np.array([[20, 21]], np.uint32), host=host)
+    ref.update(np.array([[20, 21]], np.uint32))
+    assert np.array_equal(dev.export(), ref.export())
+
+
+def test_query_pair_out_of_range():
+    V = 30
+    dev = _dev(V, 1)
+    dev.update(np.array([[0, 1]], np.uint32))
+    st, a = dev.query(np.array([[0, 1], [0, 30], [2, 3]], np.uint32))
+    assert a.tolist() == [1, 0, 0]
+    assert dev.sync() == 1
+    # an invalid query does not drop updates
+    dev.update(np.array([[2, 3]], np.uint32))
+    st, a = dev.query(np.array([[2, 3]], np.uint32))
+    assert a.tolist() == [1]
+    assert dev.sync() == 0
+
+
+def test_too_few_rounds_incomplete_matches_oracle():
+    V = 64
+    E = np.array([[i, i + 1] for i in range(V - 1)], np.uint32)
+    params = (2, 0, 0, 0)
+    dev, ref = _dev(V, 1, params), O.Graph(V, 1, L=2)
+    dev.update(E)
+    ref.update(E)
+    assert np.array_equal(dev.export(), ref.export())
+    assert_same_recovery(dev, ref)
+    assert dev.sync() == 3  # CUPC_EINCOMPLETE
+
+
+@pytest.mark.parametrize("L,Cc,D", [(4, 2, 5), (3, 1, 3), (9, 12, 20)])
+def test_parameter_overrides(L, Cc, D):
+    V = 300
+    E = WL.er_edges(V, 0.02, L * 100 + Cc)
+    dev, ref = _dev(V, 4, (L, Cc, D, 0)), O.Graph(V, 4, L=L, C=Cc, D=D)
+    assert (dev.L, dev.C, dev.D) == (L, Cc, D)
+    dev.update(E)
+    ref.update(E)
+    assert np.array_equal(dev.export(), ref.export())
+    assert_same_recovery(dev, ref)
+
+
+def test_many_components_cliques_and_bridges():
+    # scaled-down adversarial shape: disjoint cliques joined then split by
+    # bridges; a query batch after every batch
+    k, s, V = 16, 24, 16 * 24
+    perm = WL.rng(5).permutation(V).astype(np.uint32)
+    cl = []
+    for c in range(k):
+        m = perm[c * s:(c + 1) * s]
+        iu, ju = np.triu_indices(s, 1)
+        cl.append(np.stack([m[iu], m[ju]], 1))
+    cl = np.concatenate(cl)
+    g = WL.rng(6)
+    dev, ref = _dev(V, 9), O.Graph(V, 9)
+    dev.update(cl)
+    ref.update(cl)
+    comp = np.repeat(np.arange(k), s)[np.argsort(perm)]
+    bridges = []
+    while len(bridges) < 40:
+        u, v = g.integers(0, V, 2)
+        if comp[u] != comp[v]:
+            bridges.append((min(u, v), max(u, v)))
+    bridges = np.unique(np.array(bridges, np.uint32), axis=0)
+    batches = [(b, 1) for b in np.array_split(bridges, 4)] + [(b, -1) for b in np.array_split(bridges[::-1], 4)]
+    for b, op in batches:
+        ops = np.full(len(b), op, np.int8)
+        dev.update(b, ops)
+        ref.update(b, ops)
+        pairs = WL.uniform_pairs(V, 300, g, distinct=False)
+        s1, a1 = dev.query(pairs)
+        s2, a2 = ref.query(pairs)
+        assert np.array_equal(a1, a2)
+        assert_same_recovery(dev, ref)
+    assert np.array_equal(dev.labels(), min_labels(V, np.sort((cl[:, 0].astype(np.int64) * V + cl[:, 1]))))
+
+
+def test_workspace_borrowed_from_torch():
+    from paper_2509_14433_gb300 import cupc as C
+    V = 500
+    nbytes = C.cupc_workspace_bytes(V, None)
+    ws = torch.zeros(nbytes + 256, dtype=torch.uint8, device="cuda")
+    base = ws.data_ptr()
+    off = (-base) % 256
+    dev = _dev(V, 3, None, base + off)
+    ref = O.Graph(V, 3)
+    E = WL.er_edges(V, 0.01, 2)
+    dev.update(E)
+    ref.update(E)
+    assert np.array_equal(dev.export(), ref.export())
+    assert_same_recovery(dev, ref)
+    dev.close()
+    assert C.cupc_init(V, 3, None, base + off + 8, None)[0] == C.CUPC_EINVAL
