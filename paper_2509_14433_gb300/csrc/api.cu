@@ -311,7 +311,7 @@ cupc_status cupc_sync(cupc_graph* g, cupc_stream stream) {
     if (h[GC_ERR] & kErrTimeout) return CUPC_ETIMEOUT;
     return CUPC_EINVAL;
   }
-  g->last_recovery = h[GC_COMPLETE] ? CUPC_OK : CUPC_EINCOMPLETE;
+  g->last_recovery = (h[GC_RECOVERIES] == 0 || h[GC_COMPLETE]) ? CUPC_OK : CUPC_EINCOMPLETE;
   return g->last_recovery;
 }
 
@@ -333,7 +333,7 @@ cupc_status cupc_spanning_forest(cupc_graph* g, uint64_t* edge_ids_out, size_t c
                              s));
     CUPC_TRY(cudaStreamSynchronize(s));
   }
-  g->last_recovery = h[GC_COMPLETE] ? CUPC_OK : CUPC_EINCOMPLETE;
+  g->last_recovery = (h[GC_RECOVERIES] == 0 || h[GC_COMPLETE]) ? CUPC_OK : CUPC_EINCOMPLETE;
   return g->last_recovery;
 }
 
