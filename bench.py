@@ -360,15 +360,42 @@ def plain_stream_latency(torch, C, dev, stream):
             "plain_v1024_toggle_updates_per_s": n_upd / upd_t, "plain_v1024_queries": len(lat)}
 
 
+def run_apply_profile(args):
+    """Small case for ncu: a V=16384 graph (826 MB of sketches, larger than
+    L2) receives the first 8 insert batches of the dense stream."""
+    import torch
+
+    from paper_2509_14433_gb300 import cupc as C
+    torch.cuda.set_device(0)
+    E, _ = make_dense_stream()
+    n = 8 * BATCH
+    E_d = torch.from_numpy(E[:n].reshape(-1)).cuda()
+    ins_d = torch.ones(n, dtype=torch.int8, device="cuda")
+    stream = torch.cuda.current_stream()
+    st, g = C.cupc_init(V_DENSE, SEED, None, None, stream)
+    C.check(st)
+    for i in range(0, n, BATCH):
+        C.check(C.cupc_update_batch(g, E_d[2 * i:], ins_d[i:], BATCH, stream))
+    pairs = torch.from_numpy(WL.uniform_pairs(V_DENSE, 1000, WL.rng(5)).reshape(-1)).cuda()
+    out = torch.empty(1000, dtype=torch.uint8, device="cuda")
+    C.check(C.cupc_query(g, pairs, 1000, out, stream))
+    C.check(C.cupc_sync(g, stream))
+    C.cupc_destroy(g)
+    print("apply-profile done")
+
+
 def main():
     ap = argparse.ArgumentParser()
+    ap.add_argument("--mode", default="bench", choices=["bench", "apply-profile"])
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="cupc", choices=["cupc", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.mode == "apply-profile":
+        run_apply_profile(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_gpu(args)

@@ -41,7 +41,7 @@ Dims derive(uint32_t V, const cupc_params* p) {
   d.max_pairs = d.max_batch;
   if (d.C > 31 || d.D > 63 || d.D < 1 || d.L < 1 || d.L > 64) return d;
   d.W = 1 + d.C * d.D;
-  if (d.W > kRecThreads * kRecBucketsPerThread) return d;
+  if (d.W > 32 * kWarpBuckets) return d;
   // the edge index u*V+v must fit the 64-bit bucket word; record offsets are u32
   if ((uint64_t)d.max_batch * 2 >= 0xFFFFFFFFull) return d;
   d.ok = true;

@@ -30,7 +30,7 @@ constexpr uint32_t kItemRecords = 512;
 // Threads of the recovery kernel and members per reduction work item.
 constexpr uint32_t kRecThreads = 256;
 constexpr uint32_t kRecSpan = 32;
-constexpr uint32_t kRecBucketsPerThread = 2;  // W <= 512
+constexpr uint32_t kWarpBuckets = 8;  // buckets per lane in the recovery: W <= 256
 // Bounded device-side waits give up after this long.
 constexpr uint64_t kWaitLimitNs = 2000000000ull;
 

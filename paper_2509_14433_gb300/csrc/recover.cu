@@ -42,7 +42,7 @@ struct RecArgs {
 // Grid barrier for a cooperative launch. The wait is bounded: after
 // kWaitLimitNs it records kErrTimeout and returns false in every thread of
 // the CTA, which must then return.
-__device__ bool grid_barrier(uint32_t* gc, uint32_t nblocks, int* s_ok) {
+__device__ __forceinline__ bool grid_barrier(uint32_t* gc, uint32_t nblocks, int* s_ok) {
   __syncthreads();
   if (threadIdx.x == 0) {
     volatile uint32_t* gen = gc + GC_BAR_GEN;
@@ -85,37 +85,35 @@ __device__ __forceinline__ uint32_t find_root(const uint32_t* parent, uint32_t x
   return x;
 }
 
-// Sample the layer-r sum held by the CTA (thread t owns buckets t, t+256).
-// Result in s_res[0] (0 ZERO, 1 GOOD, 2 FAIL) and s_edge.
-__device__ void cta_sample(const RecArgs& a, uint32_t r, const ulonglong2 (&acc)[kRecBucketsPerThread],
-                           uint32_t* s_min, uint64_t* s_edge, uint32_t* s_res) {
-  const uint64_t kchk = a.keys[r * (a.C + 1) + a.C];
-  if (threadIdx.x == 0) *s_min = kNoneU32;
-  __syncthreads();
-  uint32_t my = kNoneU32;
+// Sample a layer-r sum held by a warp (lane l holds buckets l + 32q): ZERO
+// if the deterministic bucket is zero, else the first good bucket in index
+// order (deterministic bucket, then column-major), else FAIL. Returns 0/1/2
+// in every lane and the edge id in `edge`. Buckets after the first good one
+// are not hashed (the flag is warp-uniform).
+__device__ __forceinline__ uint32_t warp_sample(const ulonglong2 (&acc)[kWarpBuckets], uint32_t W, uint32_t V,
+                                                uint64_t kchk, uint64_t& edge) {
+  const uint32_t lane = threadIdx.x & 31;
+  if (__shfl_sync(0xffffffffu, (acc[0].x | acc[0].y) == 0 ? 1u : 0u, 0)) return 0;
+  uint32_t found = 0;
+  uint64_t e = 0;
 #pragma unroll
-  for (uint32_t q = 0; q < kRecBucketsPerThread; q++) {
-    uint32_t j = threadIdx.x + q * blockDim.x;
-    if (j < a.W && acc[q].x != 0 && mix64(acc[q].x ^ kchk) == acc[q].y) {
-      uint64_t u = acc[q].x / a.V, v = acc[q].x % a.V;
-      if (u < v && j < my) my = j;
+  for (uint32_t q = 0; q < kWarpBuckets; q++) {
+    const uint32_t j = lane + 32 * q;
+    bool good = false;
+    if (!found && j < W && acc[q].x != 0 && mix64(acc[q].x ^ kchk) == acc[q].y) good = acc[q].x / V < acc[q].x % V;
+    const uint32_t m = __ballot_sync(0xffffffffu, good);
+    const uint64_t x = __shfl_sync(0xffffffffu, acc[q].x, m ? __ffs(m) - 1 : 0);
+    if (!found && m) {
+      e = x;
+      found = 1;
     }
   }
-  if (my != kNoneU32) atomicMin(s_min, my);
-  __syncthreads();
-  const uint32_t jmin = *s_min;
-  if (threadIdx.x == 0) {
-    bool zero = (acc[0].x | acc[0].y) == 0;
-    *s_res = zero ? 0u : (jmin == kNoneU32 ? 2u : 1u);
-  }
-#pragma unroll
-  for (uint32_t q = 0; q < kRecBucketsPerThread; q++)
-    if (threadIdx.x + q * blockDim.x == jmin) *s_edge = acc[q].x;
-  __syncthreads();
+  edge = e;
+  return found ? 1u : 2u;
 }
 
-// Record the sample of component K (thread 0 only).
-__device__ void take_sample(const RecArgs& a, uint32_t r, uint32_t K, uint32_t res, uint64_t e) {
+// Record the sample of component K (one lane).
+__device__ __forceinline__ void take_sample(const RecArgs& a, uint32_t r, uint32_t K, uint32_t res, uint64_t e) {
   atomicAdd(&a.log_live[r], 1u);
   if (res == 0) {
     a.final_[K] = 1;
@@ -137,18 +135,36 @@ __device__ void take_sample(const RecArgs& a, uint32_t r, uint32_t K, uint32_t r
   }
 }
 
+__device__ __forceinline__ void warp_xor_row(ulonglong2 (&acc)[kWarpBuckets], const ulonglong2* __restrict__ row,
+                                             uint32_t W, uint32_t lane) {
+#pragma unroll
+  for (uint32_t q = 0; q < kWarpBuckets; q++) {
+    const uint32_t b = lane + 32 * q;
+    if (b < W) {
+      const ulonglong2 x = __ldg(row + b);
+      acc[q].x ^= x.x;
+      acc[q].y ^= x.y;
+    }
+  }
+}
+
 __global__ void __launch_bounds__(kRecThreads) k_recover(RecArgs a) {
   __shared__ int s_ok;
-  __shared__ uint32_t s_min, s_res, s_sum[kRecThreads / 32];
-  __shared__ uint64_t s_edge;
-  __shared__ uint32_t s_w[kRecSpan], s_k[kRecSpan];
-  const uint32_t V = a.V, nb = gridDim.x, tid = threadIdx.x;
+  const uint32_t V = a.V, W = a.W, nb = gridDim.x, tid = threadIdx.x, lane = tid & 31;
   const uint32_t gtid = blockIdx.x * blockDim.x + tid, gstride = gridDim.x * blockDim.x;
+  const uint32_t wpb = blockDim.x >> 5, gwarp = blockIdx.x * wpb + (tid >> 5), nwarps = gridDim.x * wpb;
   uint32_t* gc = a.gc;
 
   for (uint32_t w = gtid; w < V; w += gstride) {
     a.label[w] = w;
     a.final_[w] = 0;
+    a.parent[w] = w;
+    a.minv[w] = kNoneU32;
+    a.merged[w] = 0;
+    a.cand[w] = kNone;
+    a.best[w] = kNone;
+    a.tgt[w] = kNoneU32;
+    a.rcnt[w] = 0;
   }
   if (gtid == 0) {
     gc[GC_NFOREST] = 0;
@@ -157,6 +173,10 @@ __global__ void __launch_bounds__(kRecThreads) k_recover(RecArgs a) {
     gc[GC_LOGLEN] = 0;
     gc[GC_COMPLETE] = 0;
     gc[GC_ROUNDS] = 0;
+    gc[GC_NZ] = 0;
+    gc[GC_ACTIVE] = 0;
+    gc[GC_NPARTIAL] = 0;
+    gc[GC_NMEMBERS] = 0;
     gc[GC_RECOVERIES] += 1;
   }
   for (uint32_t r = gtid; r < a.L; r += gstride) {
@@ -166,168 +186,110 @@ __global__ void __launch_bounds__(kRecThreads) k_recover(RecArgs a) {
   if (!grid_barrier(gc, nb, &s_ok)) return;
 
   for (uint32_t r = 0; r < a.L; r++) {
-    // ---- reset per-round scratch
-    for (uint32_t w = gtid; w < V; w += gstride) {
-      a.parent[w] = w;
-      a.best[w] = kNone;
-      a.tgt[w] = kNoneU32;
-      a.minv[w] = kNoneU32;
-      a.merged[w] = 0;
-      a.rcnt[w] = 0;
-      a.cand[w] = kNone;
-      a.partial[w] = 0;
-    }
-    if (gtid == 0) {
-      gc[GC_NZ] = 0;
-      gc[GC_ACTIVE] = 0;
-      gc[GC_NPARTIAL] = 0;
-    }
-    if (!grid_barrier(gc, nb, &s_ok)) return;
-
-    // ---- group live vertices by component (rounds >= 1)
+    const uint64_t kchk = a.keys[r * (a.C + 1) + a.C];
+    // ---- group live vertices by component (rounds >= 1): count, allocate a
+    // segment per component, scatter
     uint32_t nmem = V;
     if (r > 0) {
       for (uint32_t w = gtid; w < V; w += gstride) {
-        uint32_t K = ld_cg(&a.label[w]);
+        a.parent[w] = w;
+        a.minv[w] = kNoneU32;
+        a.merged[w] = 0;
+        const uint32_t K = ld_cg(&a.label[w]);
         if (!ld_cg(&a.final_[K])) atomicAdd(&a.rcnt[K], 1u);
       }
       if (!grid_barrier(gc, nb, &s_ok)) return;
-      const uint32_t tile = 8 * kRecThreads, ntiles = (V + tile - 1) / tile;
-      for (uint32_t t = blockIdx.x; t < ntiles; t += nb) {
-        uint32_t sum = 0;
-        for (uint32_t k = 0; k < 8; k++) {
-          uint32_t w = t * tile + tid * 8 + k;
-          if (w < V) sum += ld_cg(&a.rcnt[w]);
-        }
-        sum = __reduce_add_sync(0xffffffffu, sum);
-        if ((tid & 31) == 0) s_sum[tid >> 5] = sum;
-        __syncthreads();
-        if (tid == 0) {
-          uint32_t tot = 0;
-          for (uint32_t k = 0; k < kRecThreads / 32; k++) tot += s_sum[k];
-          a.tilesum[t] = tot;
-        }
-        __syncthreads();
-      }
-      if (!grid_barrier(gc, nb, &s_ok)) return;
-      if (blockIdx.x == 0 && tid == 0) {
-        uint32_t run = 0;
-        for (uint32_t t = 0; t < ntiles; t++) {
-          uint32_t x = ld_cg(&a.tilesum[t]);
-          a.tilesum[t] = run;
-          run += x;
-        }
-        gc[GC_NMEMBERS] = run;
-      }
-      if (!grid_barrier(gc, nb, &s_ok)) return;
-      for (uint32_t t = blockIdx.x; t < ntiles; t += nb) {
-        uint32_t c[8], loc = 0;
-        for (uint32_t k = 0; k < 8; k++) {
-          uint32_t w = t * tile + tid * 8 + k;
-          c[k] = w < V ? ld_cg(&a.rcnt[w]) : 0;
-          loc += c[k];
-        }
-        // block exclusive scan of loc
-        const uint32_t lane = tid & 31, wid = tid >> 5;
-        uint32_t inc = loc;
+      for (uint32_t base = blockIdx.x * blockDim.x; base < V; base += gstride) {
+        const uint32_t K = base + tid;
+        const uint32_t c = K < V ? ld_cg(&a.rcnt[K]) : 0;
+        uint32_t inc = c;
+#pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-          uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+          const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
           if (lane >= (uint32_t)o) inc += y;
         }
-        if (lane == 31) s_sum[wid] = inc;
-        __syncthreads();
+        const uint32_t tot = __shfl_sync(0xffffffffu, inc, 31);
         uint32_t wbase = 0;
-        for (uint32_t k = 0; k < wid; k++) wbase += s_sum[k];
-        uint32_t run = ld_cg(&a.tilesum[t]) + wbase + inc - loc;
-        for (uint32_t k = 0; k < 8; k++) {
-          uint32_t w = t * tile + tid * 8 + k;
-          if (w < V) {
-            a.roff[w] = run;
-            a.rcnt[w] = run;  // becomes the scatter cursor, then the segment end
-          }
-          run += c[k];
+        if (lane == 31 && tot) wbase = atomicAdd(&gc[GC_NMEMBERS], tot);
+        wbase = __shfl_sync(0xffffffffu, wbase, 31);
+        if (c) {
+          a.roff[K] = wbase + inc - c;
+          a.rcnt[K] = wbase + inc - c;  // scatter cursor, then the segment end
         }
-        __syncthreads();
       }
       if (!grid_barrier(gc, nb, &s_ok)) return;
       for (uint32_t w = gtid; w < V; w += gstride) {
-        uint32_t K = ld_cg(&a.label[w]);
+        const uint32_t K = ld_cg(&a.label[w]);
         if (!ld_cg(&a.final_[K])) a.perm[atomicAdd(&a.rcnt[K], 1u)] = w;
       }
       if (!grid_barrier(gc, nb, &s_ok)) return;
       nmem = ld_cg(&gc[GC_NMEMBERS]);
     }
 
-    // ---- reduce + sample
-    const uint32_t nspans = (nmem + kRecSpan - 1) / kRecSpan;
-    for (uint32_t sp = blockIdx.x; sp < nspans; sp += nb) {
-      const uint32_t i0 = sp * kRecSpan, i1 = min(nmem, i0 + kRecSpan);
-      if (tid < i1 - i0) {
-        uint32_t w = r > 0 ? ld_cg(&a.perm[i0 + tid]) : i0 + tid;
-        s_w[tid] = w;
-        s_k[tid] = r > 0 ? ld_cg(&a.label[w]) : w;
+    // ---- reduce + sample, one warp per span of members; round 0 has one
+    // vertex per span (every vertex is its own component)
+    const uint32_t span = r == 0 ? 1u : kRecSpan;
+    const uint32_t nspans = (nmem + span - 1) / span;
+    for (uint32_t sp = gwarp; sp < nspans; sp += nwarps) {
+      const uint32_t i0 = sp * span, cnt = min(span, nmem - i0);
+      uint32_t mw = 0, mk = kNoneU32;
+      if (lane < cnt) {
+        mw = r > 0 ? ld_cg(&a.perm[i0 + lane]) : i0 + lane;
+        mk = r > 0 ? ld_cg(&a.label[mw]) : mw;
       }
-      __syncthreads();
-      ulonglong2 acc[kRecBucketsPerThread];
-      uint32_t i = i0;
-      while (i < i1) {
-        const uint32_t K = s_k[i - i0];
-        uint32_t j = i;
-        while (j < i1 && s_k[j - i0] == K) j++;
+      uint32_t i = 0;
+      while (i < cnt) {
+        const uint32_t K = __shfl_sync(0xffffffffu, mk, i);
+        const uint32_t rest = ~(__ballot_sync(0xffffffffu, mk == K) >> i);
+        const uint32_t j = i + (rest ? (uint32_t)__ffs(rest) - 1 : 32 - i);
+        ulonglong2 acc[kWarpBuckets];
 #pragma unroll
-        for (uint32_t q = 0; q < kRecBucketsPerThread; q++) acc[q] = make_ulonglong2(0, 0);
+        for (uint32_t q = 0; q < kWarpBuckets; q++) acc[q] = make_ulonglong2(0, 0);
         for (uint32_t m = i; m < j; m++) {
-          const ulonglong2* row = a.sketch + ((size_t)r * V + s_w[m - i0]) * a.W;
-#pragma unroll
-          for (uint32_t q = 0; q < kRecBucketsPerThread; q++) {
-            uint32_t b = tid + q * kRecThreads;
-            if (b < a.W) {
-              ulonglong2 x = __ldg(row + b);
-              acc[q].x ^= x.x;
-              acc[q].y ^= x.y;
-            }
-          }
+          const uint32_t w = __shfl_sync(0xffffffffu, mw, m);
+          warp_xor_row(acc, a.sketch + ((size_t)r * V + w) * W, W, lane);
         }
-        const bool whole = r == 0 || (ld_cg(&a.roff[K]) == i && ld_cg(&a.rcnt[K]) == j);
+        const bool whole = r == 0 || (ld_cg(&a.roff[K]) == i0 + i && ld_cg(&a.rcnt[K]) == i0 + j);
         if (whole) {
-          cta_sample(a, r, acc, &s_min, &s_edge, &s_res);
-          if (tid == 0) take_sample(a, r, K, s_res, s_edge);
+          uint64_t e = 0;
+          const uint32_t res = warp_sample(acc, W, V, kchk, e);
+          if (lane == 0) take_sample(a, r, K, res, e);
         } else {
-          ulonglong2* dst = a.acc + (size_t)K * a.W;
+          ulonglong2* dst = a.acc + (size_t)K * W;
 #pragma unroll
-          for (uint32_t q = 0; q < kRecBucketsPerThread; q++) {
-            uint32_t b = tid + q * kRecThreads;
-            if (b < a.W && (acc[q].x | acc[q].y)) {
+          for (uint32_t q = 0; q < kWarpBuckets; q++) {
+            const uint32_t b = lane + 32 * q;
+            if (b < W && (acc[q].x | acc[q].y)) {
               atomicXor(&dst[b].x, acc[q].x);
               atomicXor(&dst[b].y, acc[q].y);
             }
           }
           // the span holding the component's first member lists it once
-          if (tid == 0 && ld_cg(&a.roff[K]) == i) a.plist[atomicAdd(&gc[GC_NPARTIAL], 1u)] = K;
+          if (lane == 0 && ld_cg(&a.roff[K]) == i0 + i) a.plist[atomicAdd(&gc[GC_NPARTIAL], 1u)] = K;
         }
         i = j;
       }
-      __syncthreads();
     }
     if (!grid_barrier(gc, nb, &s_ok)) return;
 
-    // ---- sample components spread over several spans
+    // ---- sample components spread over several spans, one warp each
     const uint32_t npart = ld_cg(&gc[GC_NPARTIAL]);
-    for (uint32_t p = blockIdx.x; p < npart; p += nb) {
+    for (uint32_t p = gwarp; p < npart; p += nwarps) {
       const uint32_t K = ld_cg(&a.plist[p]);
-      ulonglong2* src = a.acc + (size_t)K * a.W;
-      ulonglong2 acc[kRecBucketsPerThread];
+      ulonglong2* src = a.acc + (size_t)K * W;
+      ulonglong2 acc[kWarpBuckets];
 #pragma unroll
-      for (uint32_t q = 0; q < kRecBucketsPerThread; q++) {
-        uint32_t b = tid + q * kRecThreads;
+      for (uint32_t q = 0; q < kWarpBuckets; q++) {
+        const uint32_t b = lane + 32 * q;
         acc[q] = make_ulonglong2(0, 0);
-        if (b < a.W) {
+        if (b < W) {
           acc[q] = __ldcg(src + b);
           src[b] = make_ulonglong2(0, 0);
         }
       }
-      cta_sample(a, r, acc, &s_min, &s_edge, &s_res);
-      if (tid == 0) take_sample(a, r, K, s_res, s_edge);
+      uint64_t e = 0;
+      const uint32_t res = warp_sample(acc, W, V, kchk, e);
+      if (lane == 0) take_sample(a, r, K, res, e);
     }
     if (!grid_barrier(gc, nb, &s_ok)) return;
     if (gtid == 0) gc[GC_ROUNDS] = r + 1;
@@ -339,10 +301,10 @@ __global__ void __launch_bounds__(kRecThreads) k_recover(RecArgs a) {
     // ---- hook: minimum spanning forest of the candidates (Boruvka)
     for (uint32_t iter = 0; iter < 64; iter++) {
       for (uint32_t K = gtid; K < V; K += gstride) {
-        uint64_t e = ld_cg(&a.cand[K]);
+        const uint64_t e = ld_cg(&a.cand[K]);
         if (e == kNone) continue;
-        uint32_t ra = find_root(a.parent, ld_cg(&a.label[(uint32_t)(e / V)]), V);
-        uint32_t rb = find_root(a.parent, ld_cg(&a.label[(uint32_t)(e % V)]), V);
+        const uint32_t ra = find_root(a.parent, ld_cg(&a.label[(uint32_t)(e / V)]), V);
+        const uint32_t rb = find_root(a.parent, ld_cg(&a.label[(uint32_t)(e % V)]), V);
         if (ra != rb) {
           atomicMin((unsigned long long*)&a.best[ra], (unsigned long long)e);
           atomicMin((unsigned long long*)&a.best[rb], (unsigned long long)e);
@@ -352,26 +314,25 @@ __global__ void __launch_bounds__(kRecThreads) k_recover(RecArgs a) {
       if (!grid_barrier(gc, nb, &s_ok)) return;
       if (ld_cg(&gc[GC_ACTIVE]) == 0) break;
       for (uint32_t x = gtid; x < V; x += gstride) {
-        uint64_t e = ld_cg(&a.best[x]);
+        const uint64_t e = ld_cg(&a.best[x]);
         if (e == kNone) continue;
-        uint32_t ra = find_root(a.parent, ld_cg(&a.label[(uint32_t)(e / V)]), V);
-        uint32_t rb = find_root(a.parent, ld_cg(&a.label[(uint32_t)(e % V)]), V);
+        const uint32_t ra = find_root(a.parent, ld_cg(&a.label[(uint32_t)(e / V)]), V);
+        const uint32_t rb = find_root(a.parent, ld_cg(&a.label[(uint32_t)(e % V)]), V);
         a.tgt[x] = ra == x ? rb : ra;
       }
       if (!grid_barrier(gc, nb, &s_ok)) return;
       for (uint32_t x = gtid; x < V; x += gstride) {
-        uint32_t o = ld_cg(&a.tgt[x]);
+        const uint32_t o = ld_cg(&a.tgt[x]);
         if (o == kNoneU32) continue;
-        uint64_t e = ld_cg(&a.best[x]);
-        bool mutual = ld_cg(&a.tgt[o]) == x;
+        const bool mutual = ld_cg(&a.tgt[o]) == x;
         if (!mutual || x > o) {
           a.parent[x] = o;
-          a.forest[atomicAdd(&gc[GC_NFOREST], 1u)] = e;
+          a.forest[atomicAdd(&gc[GC_NFOREST], 1u)] = ld_cg(&a.best[x]);
         }
       }
       if (!grid_barrier(gc, nb, &s_ok)) return;
       for (uint32_t x = gtid; x < V; x += gstride) {
-        uint32_t p = ld_cg(&a.parent[x]);
+        const uint32_t p = ld_cg(&a.parent[x]);
         if (p != x) a.parent[x] = find_root(a.parent, p, V);
         a.best[x] = kNone;
         a.tgt[x] = kNoneU32;
@@ -380,18 +341,26 @@ __global__ void __launch_bounds__(kRecThreads) k_recover(RecArgs a) {
       if (!grid_barrier(gc, nb, &s_ok)) return;
     }
 
-    // ---- relabel to the minimum vertex id of each component
+    // ---- relabel to the minimum vertex id of each component; clear the
+    // round's scratch for the next round
     for (uint32_t w = gtid; w < V; w += gstride) {
+      a.rcnt[w] = 0;
+      a.cand[w] = kNone;
       if (ld_cg(&a.label[w]) != w) continue;
-      uint32_t root = ld_cg(&a.parent[w]);
+      const uint32_t root = ld_cg(&a.parent[w]);
       atomicMin(&a.minv[root], w);
       if (root != w) a.merged[root] = 1;
     }
+    if (gtid == 0) {
+      gc[GC_NZ] = 0;
+      gc[GC_NPARTIAL] = 0;
+      gc[GC_NMEMBERS] = 0;
+    }
     if (!grid_barrier(gc, nb, &s_ok)) return;
     for (uint32_t w = gtid; w < V; w += gstride) {
-      uint32_t K = ld_cg(&a.label[w]);
-      uint32_t root = ld_cg(&a.parent[K]);
-      uint32_t nl = ld_cg(&a.minv[root]);
+      const uint32_t K = ld_cg(&a.label[w]);
+      const uint32_t root = ld_cg(&a.parent[K]);
+      const uint32_t nl = ld_cg(&a.minv[root]);
       a.label[w] = nl;
       if (w == root && ld_cg(&a.merged[root])) a.final_[nl] = 0;
     }

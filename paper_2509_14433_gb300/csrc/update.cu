@@ -164,31 +164,47 @@ __device__ __forceinline__ void xor_bucket_atomic(ulonglong2* p, ulonglong2 v) {
   atomicXor(&p->y, v.y);
 }
 
+// The SplitMix64 finalizer of idx ^ key, split so that its first step is
+// shared by every lane: with z = idx ^ key, z ^ (z >> 30) equals
+// pre(idx) ^ pre(key), pre(x) = x ^ (x >> 30), because XOR commutes with a
+// logical shift. pre(idx) is computed once per record when the record is
+// staged in shared memory; pre(key) is a per-lane constant.
+__device__ __forceinline__ uint64_t pre_mix(uint64_t x) { return x ^ (x >> 30); }
+__device__ __forceinline__ uint64_t mix_tail(uint64_t z) {
+  z *= 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
 // Fold the records of one work item into the sketches of its vertex.
 // Thread layout: tid = r*P + s; r < L is the layer, s < C a column, s == C
-// the checksum lane (owner of the deterministic bucket). A lane is the only
-// writer of its column's shared-memory rows, so no shared atomics are
-// needed; the checksum of a record reaches the column lanes by shuffle.
+// the checksum lane, which owns the deterministic bucket (its row 0). A lane
+// is the only writer of its rows in shared memory, so no shared atomics are
+// needed, and every active lane runs the same instruction stream; the
+// checksum of a record reaches the column lanes by shuffle.
 __global__ void k_apply(ulonglong2* __restrict__ sketch, const uint64_t* __restrict__ keys,
                         const uint64_t* __restrict__ rec, const uint4* __restrict__ items, uint32_t* gc,
                         uint32_t V, uint32_t L, uint32_t C, uint32_t D, uint32_t W, uint32_t P, uint32_t R) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   uint64_t* s_rec = reinterpret_cast<uint64_t*>(smem_raw);
-  ulonglong2* s_acc = reinterpret_cast<ulonglong2*>(smem_raw + kItemRecords * sizeof(uint64_t));
+  uint64_t* s_pre = s_rec + kItemRecords;
+  ulonglong2* s_acc = reinterpret_cast<ulonglong2*>(s_pre + kItemRecords);
   __shared__ uint32_t s_item;
 
   if (ld_cg(&gc[GC_ERR]) & kErrInval) return;
   const uint32_t tid = threadIdx.x, lane = tid & 31;
   const uint32_t r = tid / P, s = tid % P;
-  const bool in_layer = r < L;
-  const bool is_col = in_layer && s < C;
-  const bool is_chk = in_layer && s == C;
-  const uint64_t key = (in_layer && s <= C) ? keys[r * (C + 1) + s] : 0;
+  const bool active = r < L && s <= C;
+  const bool is_chk = s == C;
+  const uint64_t kpre = active ? pre_mix(keys[r * (C + 1) + s]) : 0;
   const uint32_t chk_lane = (lane & ~(P - 1)) | C;
-  ulonglong2* my_rows = s_acc + ((size_t)(in_layer ? r : 0) * C + (s < C ? s : 0)) * R;
-
-  if (is_col)
-    for (uint32_t d = 0; d < R; d++) my_rows[d] = make_ulonglong2(0, 0);
+  const uint32_t jbase = is_chk ? 0u : 1u + s * D;  // first bucket of this lane's column
+  const uint32_t nrows = is_chk ? 1u : R;
+  // row d of this lane lives at s_acc[d * blockDim.x + tid]: the 8 lanes of a
+  // shared-memory phase always hit 8 distinct 16-byte bank groups
+  ulonglong2* my_rows = s_acc + tid;
+  const uint32_t rs = blockDim.x;
+  for (uint32_t d = 0; d < R; d++) my_rows[d * rs] = make_ulonglong2(0, 0);
 
   const uint32_t nitems = ld_cg(&gc[GC_NITEMS]);
   for (;;) {
@@ -199,12 +215,14 @@ __global__ void k_apply(ulonglong2* __restrict__ sketch, const uint64_t* __restr
     const uint4 item = items[it];
     const uint32_t w = item.x, beg = item.y, n = item.z - item.y;
     const bool excl = item.w != 0;
-    for (uint32_t i = tid; i < n; i += blockDim.x) s_rec[i] = rec[beg + i];
+    for (uint32_t i = tid; i < n; i += blockDim.x) {
+      const uint64_t x = rec[beg + i];
+      s_rec[i] = x;
+      s_pre[i] = pre_mix(x);
+    }
     __syncthreads();
 
-    ulonglong2* gv = sketch + ((size_t)(in_layer ? r : 0) * V + w) * W;
-    uint64_t det_a = 0, det_g = 0;
-    uint32_t mask = 0;
+    ulonglong2* gb = sketch + ((size_t)(r < L ? r : 0) * V + w) * W + jbase;
     uint32_t i = 0;
     // four records per step: four independent hash chains per lane
     for (; i + 4 <= n; i += 4) {
@@ -212,91 +230,73 @@ __global__ void k_apply(ulonglong2* __restrict__ sketch, const uint64_t* __restr
 #pragma unroll
       for (int k = 0; k < 4; k++) {
         x[k] = s_rec[i + k];
-        h[k] = mix64(x[k] ^ key);
+        h[k] = mix_tail(s_pre[i + k] ^ kpre);
       }
 #pragma unroll
       for (int k = 0; k < 4; k++) gm[k] = __shfl_sync(0xffffffffu, h[k], chk_lane);
 #pragma unroll
       for (int k = 0; k < 4; k++) {
-        if (is_chk) {
-          det_a ^= x[k];
-          det_g ^= h[k];
-        } else if (is_col) {
-          uint32_t d = depth_of(h[k], D);
+        const uint32_t lo = (uint32_t)h[k];
+        uint32_t d = (uint32_t)__ffs(lo) - 1;
+        if (lo == 0) d = depth_of(h[k], D);
+        d = min(d, D - 1);
+        if (is_chk) d = 0;
+        if (active) {
           if (d < R) {
-            ulonglong2 v = my_rows[d];
+            ulonglong2 v = my_rows[d * rs];
             v.x ^= x[k];
             v.y ^= gm[k];
-            my_rows[d] = v;
-            mask |= 1u << d;
+            my_rows[d * rs] = v;
           } else {
-            xor_bucket_atomic(gv + 1 + s * D + d, make_ulonglong2(x[k], gm[k]));
+            xor_bucket_atomic(gb + d, make_ulonglong2(x[k], gm[k]));
           }
         }
       }
     }
     for (; i < n; i++) {
-      uint64_t x = s_rec[i];
-      uint64_t h = mix64(x ^ key);
-      uint64_t gm = __shfl_sync(0xffffffffu, h, chk_lane);
-      if (is_chk) {
-        det_a ^= x;
-        det_g ^= h;
-      } else if (is_col) {
-        uint32_t d = depth_of(h, D);
+      const uint64_t x = s_rec[i];
+      const uint64_t h = mix_tail(s_pre[i] ^ kpre);
+      const uint64_t gm = __shfl_sync(0xffffffffu, h, chk_lane);
+      uint32_t d = is_chk ? 0u : depth_of(h, D);
+      if (active) {
         if (d < R) {
-          ulonglong2 v = my_rows[d];
+          ulonglong2 v = my_rows[d * rs];
           v.x ^= x;
           v.y ^= gm;
-          my_rows[d] = v;
-          mask |= 1u << d;
+          my_rows[d * rs] = v;
         } else {
-          xor_bucket_atomic(gv + 1 + s * D + d, make_ulonglong2(x, gm));
+          xor_bucket_atomic(gb + d, make_ulonglong2(x, gm));
         }
       }
     }
 
-    // write back only the touched buckets of this vertex
-    if (is_chk && (det_a | det_g)) {
-      if (excl) {
-        ulonglong2 o = __ldcg(gv);
-        o.x ^= det_a;
-        o.y ^= det_g;
-        gv[0] = o;
-      } else {
-        xor_bucket_atomic(gv, make_ulonglong2(det_a, det_g));
-      }
-    }
-    if (is_col) {
-      ulonglong2* gcol = gv + 1 + s * D;
-      while (mask) {
-        uint32_t dd[4];
+    // write back only the touched (non-zero) rows of this vertex
+    if (active) {
+      for (uint32_t d0 = 0; d0 < nrows; d0 += 4) {
         ulonglong2 v[4], o[4];
-        int k = 0;
+        bool nz[4];
 #pragma unroll
-        for (int q = 0; q < 4; q++) {
-          dd[q] = kNoneU32;
-          if (mask) {
-            dd[q] = __ffs(mask) - 1;
-            mask &= mask - 1;
-            v[q] = my_rows[dd[q]];
-            my_rows[dd[q]] = make_ulonglong2(0, 0);
-            k++;
+        for (uint32_t q = 0; q < 4; q++) {
+          const uint32_t d = d0 + q;
+          nz[q] = false;
+          if (d < nrows) {
+            v[q] = my_rows[d * rs];
+            nz[q] = (v[q].x | v[q].y) != 0;
+            if (nz[q]) my_rows[d * rs] = make_ulonglong2(0, 0);
           }
         }
         if (excl) {
 #pragma unroll
-          for (int q = 0; q < 4; q++)
-            if (dd[q] != kNoneU32) o[q] = __ldcg(gcol + dd[q]);
+          for (uint32_t q = 0; q < 4; q++)
+            if (nz[q]) o[q] = __ldcg(gb + d0 + q);
 #pragma unroll
-          for (int q = 0; q < 4; q++)
-            if (dd[q] != kNoneU32) gcol[dd[q]] = make_ulonglong2(o[q].x ^ v[q].x, o[q].y ^ v[q].y);
+          for (uint32_t q = 0; q < 4; q++)
+            if (nz[q]) gb[d0 + q] = make_ulonglong2(o[q].x ^ v[q].x, o[q].y ^ v[q].y);
         } else {
 #pragma unroll
-          for (int q = 0; q < 4; q++)
-            if (dd[q] != kNoneU32) xor_bucket_atomic(gcol + dd[q], v[q]);
+          for (uint32_t q = 0; q < 4; q++)
+            if (nz[q]) xor_bucket_atomic(gb + d0 + q, v[q]);
         }
-        (void)k;
       }
     }
     __syncthreads();
@@ -308,7 +308,7 @@ cudaError_t setup_update(cupc_graph* g) {
   while (g->P < g->C + 1) g->P <<= 1;
   g->R = g->D < kSmemRows ? g->D : kSmemRows;
   g->apply_threads = (int)(((g->L * g->P) + 31) / 32 * 32);
-  g->apply_smem = (int)(kItemRecords * sizeof(uint64_t) + (size_t)g->L * g->C * g->R * sizeof(ulonglong2));
+  g->apply_smem = (int)(2 * kItemRecords * sizeof(uint64_t) + (size_t)g->R * g->apply_threads * sizeof(ulonglong2));
   cudaError_t e = cudaFuncSetAttribute(k_apply, cudaFuncAttributeMaxDynamicSharedMemorySize, g->apply_smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;

@@ -52,7 +52,7 @@ def test_workspace_bytes(C):
         assert b % 256 == 0
     assert C.cupc_workspace_bytes(1000, (0, 32, 0, 0)) == 0  # C > 31
     assert C.cupc_workspace_bytes(1000, (0, 0, 64, 0)) == 0  # D > 63
-    assert C.cupc_workspace_bytes(1000, (0, 31, 30, 0)) == 0  # W > 512
+    assert C.cupc_workspace_bytes(1000, (0, 31, 30, 0)) == 0  # W > 256
     assert C.cupc_workspace_bytes(1000, (3, 2, 5, 100)) > 0
     assert C.cupc_workspace_bytes(1000, (0, 0, 0, 1 << 20)) > C.cupc_workspace_bytes(1000, (0, 0, 0, 1 << 10))
 
