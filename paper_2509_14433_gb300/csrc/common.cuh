@@ -177,6 +177,7 @@ cudaError_t launch_keys(cupc_graph* g, cudaStream_t s);
 cudaError_t launch_update_chunk(cupc_graph* g, const uint32_t* edges, size_t n, cudaStream_t s);
 cudaError_t launch_validate(cupc_graph* g, const uint32_t* edges, const int8_t* ops, size_t n, cudaStream_t s);
 cudaError_t setup_update(cupc_graph* g);
+cudaError_t raise_apply_smem_limit(int bytes);
 cudaError_t setup_recover(cupc_graph* g);
 cudaError_t launch_recover(cupc_graph* g, cudaStream_t s);
 cudaError_t launch_query(cupc_graph* g, const uint32_t* pairs, size_t m, uint8_t* out, cudaStream_t s);

@@ -303,13 +303,24 @@ __global__ void k_apply(ulonglong2* __restrict__ sketch, const uint64_t* __restr
   }
 }
 
+// The dynamic shared-memory limit of k_apply is process-wide: only ever
+// raise it, so that a graph created later never shrinks it below what an
+// earlier graph's launches need.
+cudaError_t raise_apply_smem_limit(int bytes) {
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, k_apply);
+  if (e != cudaSuccess) return e;
+  if (fa.maxDynamicSharedSizeBytes >= bytes) return cudaSuccess;
+  return cudaFuncSetAttribute(k_apply, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
 cudaError_t setup_update(cupc_graph* g) {
   g->P = 1;
   while (g->P < g->C + 1) g->P <<= 1;
   g->R = g->D < kSmemRows ? g->D : kSmemRows;
   g->apply_threads = (int)(((g->L * g->P) + 31) / 32 * 32);
   g->apply_smem = (int)(2 * kItemRecords * sizeof(uint64_t) + (size_t)g->R * g->apply_threads * sizeof(ulonglong2));
-  cudaError_t e = cudaFuncSetAttribute(k_apply, cudaFuncAttributeMaxDynamicSharedMemorySize, g->apply_smem);
+  cudaError_t e = raise_apply_smem_limit(g->apply_smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_apply, g->apply_threads, g->apply_smem);

@@ -268,3 +268,19 @@ def test_workspace_borrowed_from_torch():
     assert_same_recovery(dev, ref)
     dev.close()
     assert C.cupc_init(V, 3, None, base + off + 8, None)[0] == C.CUPC_EINVAL
+
+
+def test_smaller_graph_does_not_shrink_an_earlier_graphs_launch():
+    # the apply kernel's shared-memory limit is process-wide; a graph that
+    # needs less must not lower it under one that needs more
+    big = (20, 12, 0, 0)  # 20 layers x 16 lanes: > 48 KB of dynamic shared memory
+    V = 400
+    E = WL.er_edges(V, 0.02, 31)
+    dev_big, ref = _dev(V, 7, big), O.Graph(V, 7, L=20, C=12)
+    small = _dev(100, 1)
+    small.update(np.array([[1, 2]], np.uint32))
+    assert dev_big.update(E) == 0
+    ref.update(E)
+    assert dev_big.sync() == 0
+    assert np.array_equal(dev_big.export(), ref.export())
+    assert_same_recovery(dev_big, ref)
