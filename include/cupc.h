@@ -154,6 +154,33 @@ cupc_status cupc_get_params(const cupc_graph* g, uint32_t* out4);
 void cupc_destroy(cupc_graph* g);
 const char* cupc_status_string(cupc_status s);
 
+/* ---- Update without any device allocation (the paper has no counterpart).
+ *
+ * For callers that cannot call cudaMalloc at all: code whose device memory
+ * is owned entirely by another allocator (a framework's caching pool or a
+ * fixed arena), or a latency-critical path that must not pay an allocation's
+ * implicit device synchronisation. cupc_init allocates (or borrows) a
+ * workspace; this call instead applies n edge updates (same rules as
+ * cupc_update_batch, default parameters for V) to a sketch buffer the caller
+ * owns, `sketch`, laid out exactly as cupc_export_sketches writes it
+ * (L*V*W*16 bytes, device memory, zero = the empty graph), hashed with
+ * `seed`. edges/ops must be device pointers. Its scratch is one static
+ * device array of fixed size in the library (about 2.6 MB per GPU that loads
+ * the library, held until the process exits), so it accepts at most
+ * CUPC_STATIC_MAX_V vertices and CUPC_STATIC_MAX_EDGES edges per call and
+ * returns CUPC_EINVAL beyond that, before any work. The first call on a
+ * device sets up that device (looks up the array's device address and the
+ * kernel's launch shape) with the device current; make that first call
+ * before any stream capture. Every call on a device shares the one array
+ * and clears what must start at zero; calls whose work overlaps on the GPU
+ * (other streams, other host threads) race on it, so order them. An invalid
+ * edge drops the whole batch; status_out (nullable, device or host) receives
+ * the error bits of this call (0 = applied, 1 = dropped), stream-ordered. */
+#define CUPC_STATIC_MAX_V 65536u
+#define CUPC_STATIC_MAX_EDGES 65536u
+cupc_status cupc_update_sketch_static(void* sketch, uint32_t V, uint64_t seed, const uint32_t* edges,
+                                      const int8_t* ops, size_t n, uint32_t* status_out, cupc_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -48,6 +48,7 @@ _SIGS = {
     "cupc_profile_read": (ctypes.c_int, [_P, _P, _P, _sz]),
     "cupc_destroy": (None, [_P]),
     "cupc_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "cupc_update_sketch_static": (ctypes.c_int, [_P, _u32, _u64, _P, _P, _sz, _P, _P]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _fn = getattr(_lib, _name)
@@ -160,6 +161,15 @@ def cupc_destroy(g) -> None:
 
 def cupc_status_string(st: int) -> str:
     return _lib.cupc_status_string(st).decode()
+
+
+CUPC_STATIC_MAX_V = 65536
+CUPC_STATIC_MAX_EDGES = 65536
+
+
+def cupc_update_sketch_static(sketch, V: int, seed: int, edges, ops, n: int, status_out=None, stream=None) -> int:
+    return _lib.cupc_update_sketch_static(ptr(sketch), V, seed & (2**64 - 1), ptr(edges), ptr(ops), n,
+                                          ptr(status_out), stream_handle(stream))
 
 
 class CupcError(RuntimeError):
