@@ -68,6 +68,23 @@ def expected_touched_buckets(counts, L, C, D):
     return float(L * (mult * (1.0 + C * per_col)).sum())
 
 
+def apply_traffic():
+    """DRAM bytes per k_apply launch from the committed ncu summary, scaled
+    to a 2^20-edge batch; None when the kernel source changed since the
+    counters were taken."""
+    import hashlib
+    tp = os.path.join(ROOT, "profiles", "k_apply_traffic.json")
+    src = os.path.join(ROOT, "paper_2509_14433_gb300", "csrc", "update.cu")
+    try:
+        rec = json.load(open(tp))
+        md5 = hashlib.md5(open(src, "rb").read()).hexdigest()
+    except (OSError, ValueError):
+        return None
+    if rec.get("update_cu_md5") != md5:
+        return None
+    return rec.get("bytes_per_launch")
+
+
 class Clocks:
     """nvidia-smi samples during the timed region."""
 
@@ -279,13 +296,7 @@ def run_gpu(args):
         pass
     peak = float(peaks.get("hbm_gbs", 6800.0))
     achieved = apply_bytes_per_launch / (apply_ms * 1e-3) / 1e9
-    traffic = None
-    tp = os.path.join(ROOT, "profiles", "apply_traffic.json")
-    if os.path.exists(tp):
-        try:
-            traffic = json.load(open(tp)).get("bytes_per_launch")
-        except (OSError, ValueError):
-            traffic = None
+    traffic = apply_traffic()
     gpu_launches = int(nl_prof.sum())
     shares = {name: round(float(ms_prof[k]) / max(1e-9, float(ms_prof.sum())), 4)
               for k, name in enumerate(["validate", "group", "apply", "recover", "query", "sort"])}

@@ -115,3 +115,133 @@ def final_edge_set(V: int, steps) -> np.ndarray:
         for x in idx.tolist():
             present[x] = not present.get(x, False)
     return np.array(sorted(k for k, v in present.items() if v), dtype=np.uint64)
+
+
+# ---- R-MAT stream with deletes and uneven batches (torch; any device) -------
+
+def rmat_pairs(n: int, levels: int, probs, gen, device):
+    """n R-MAT pairs over 2^levels vertices (Chakrabarti, Zhan, Faloutsos,
+    SDM 2004): at each level pick quadrant a/b/c/d, i.e. (row bit, column bit)
+    = (0,0)/(0,1)/(1,0)/(1,1). Returns int64 tensors (u, v)."""
+    import torch
+    a, b, c, _ = probs
+    u = torch.zeros(n, dtype=torch.int64, device=device)
+    v = torch.zeros(n, dtype=torch.int64, device=device)
+    for _ in range(levels):
+        r = torch.rand(n, generator=gen, device=device)
+        q = (r >= a).long() + (r >= a + b).long() + (r >= a + b + c).long()
+        u = u * 2 + (q >> 1)
+        v = v * 2 + (q & 1)
+    return u, v
+
+
+class RmatStream:
+    """Batches of a valid insert/delete stream on V = 2^levels vertices.
+
+    Each batch has a size drawn log-uniformly in [batch_lo, batch_hi]; a
+    fraction `del_frac` of it deletes edges inserted by earlier batches
+    (positions drawn uniformly from the append-only list of inserted edges and
+    kept if the edge is still present), the rest inserts R-MAT edges
+    (self-loops and edges already present or repeated in the batch are
+    redrawn, up to 64 times, then replaced by uniform absent pairs; the count
+    of those fallbacks is kept). Within a batch the deletes come first, so
+    applying the batch in order keeps the stream valid. Presence is a V^2-bit
+    bitmap (2 GiB at V = 2^17) on the same device."""
+
+    def __init__(self, levels: int = 17, seed: int = 1, probs=(0.57, 0.19, 0.19, 0.05),
+                 batch_lo: int = 1000, batch_hi: int = 4 << 20, del_frac: float = 0.2, device="cpu"):
+        import torch
+        self.torch = torch
+        self.levels, self.V = levels, 1 << levels
+        self.probs, self.lo, self.hi, self.del_frac = probs, batch_lo, batch_hi, del_frac
+        self.device = torch.device(device)
+        self.gen = torch.Generator(device=self.device).manual_seed(seed)
+        nbits = self.V * self.V
+        self.bitmap = torch.zeros((nbits + 63) // 64, dtype=torch.int64, device=self.device)
+        self.inserted = []  # append-only id tensors
+        self.n_inserted = 0
+        self.fallbacks = 0
+
+    def _bits(self, ids):
+        return (self.bitmap[ids >> 6] >> (ids & 63)) & 1
+
+    def _flip(self, ids, sign):
+        one = self.torch.ones_like(ids)
+        self.bitmap.index_put_((ids >> 6,), sign * (one << (ids & 63)), accumulate=True)
+
+    def _unique_keep(self, ids):
+        u, inv = self.torch.unique(ids, return_inverse=True)
+        first = self.torch.full((u.numel(),), ids.numel(), dtype=self.torch.int64, device=self.device)
+        first.scatter_reduce_(0, inv, self.torch.arange(ids.numel(), device=self.device), "amin")
+        keep = self.torch.zeros(ids.numel(), dtype=self.torch.bool, device=self.device)
+        keep[first] = True
+        return keep
+
+    def next_size(self) -> int:
+        t = self.torch
+        x = t.rand(1, generator=self.gen, device=self.device).item()
+        return int(np.exp(np.log(self.lo) + x * (np.log(self.hi) - np.log(self.lo))))
+
+    def _deletes(self, k):
+        t = self.torch
+        if k == 0 or self.n_inserted == 0:
+            return t.zeros(0, dtype=t.int64, device=self.device)
+        pool = t.cat(self.inserted) if len(self.inserted) > 1 else self.inserted[0]
+        self.inserted = [pool]
+        got = t.zeros(0, dtype=t.int64, device=self.device)
+        for _ in range(64):
+            need = k - got.numel()
+            if need <= 0:
+                break
+            pos = t.randint(0, pool.numel(), (2 * need + 16,), generator=self.gen, device=self.device)
+            ids = pool[pos]
+            ids = ids[self._bits(ids) == 1]
+            ids = t.cat([got, ids])
+            ids = ids[self._unique_keep(ids)]
+            got = ids[:k]
+        self._flip(got, -1)
+        return got
+
+    def _inserts(self, k):
+        t = self.torch
+        got = t.zeros(0, dtype=t.int64, device=self.device)
+        for _ in range(64):
+            need = k - got.numel()
+            if need <= 0:
+                break
+            u, v = rmat_pairs(need, self.levels, self.probs, self.gen, self.device)
+            ok = u != v
+            a, b = t.minimum(u, v)[ok], t.maximum(u, v)[ok]
+            ids = a * self.V + b
+            ids = ids[self._bits(ids) == 0]
+            ids = t.cat([got, ids])
+            got = ids[self._unique_keep(ids)]
+        while got.numel() < k:  # uniform absent pairs
+            need = k - got.numel()
+            u = t.randint(0, self.V, (need,), generator=self.gen, device=self.device)
+            v = t.randint(0, self.V, (need,), generator=self.gen, device=self.device)
+            ok = u != v
+            ids = t.minimum(u, v)[ok] * self.V + t.maximum(u, v)[ok]
+            ids = ids[self._bits(ids) == 0]
+            before = got.numel()
+            got = t.cat([got, ids])
+            got = got[self._unique_keep(got)]
+            self.fallbacks += got.numel() - before
+        got = got[:k]
+        self._flip(got, 1)
+        self.inserted.append(got)
+        self.n_inserted += got.numel()
+        return got
+
+    def next_batch(self, size: int | None = None):
+        """Returns (edges int32 [n, 2], ops int8 [n]) on the stream's device."""
+        t = self.torch
+        n = self.next_size() if size is None else size
+        k_del = int(round(self.del_frac * n)) if self.n_inserted else 0
+        dels = self._deletes(k_del)
+        ins = self._inserts(n - dels.numel())
+        ids = t.cat([dels, ins])
+        edges = t.stack([ids // self.V, ids % self.V], 1).to(t.int32)
+        ops = t.cat([t.full((dels.numel(),), -1, dtype=t.int8, device=self.device),
+                     t.ones(ins.numel(), dtype=t.int8, device=self.device)])
+        return edges, ops
