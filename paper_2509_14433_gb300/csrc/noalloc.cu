@@ -105,7 +105,7 @@ extern "C" cupc_status cupc_update_sketch_static(void* sketch, uint32_t V, uint6
   g.P = ds->P;
   g.R = g.D < kSmemRows ? g.D : kSmemRows;
   g.apply_threads = (int)(((g.L * g.P) + 31) / 32 * 32);
-  g.apply_smem = (int)(2 * kItemRecords * sizeof(uint64_t) + (size_t)g.R * g.apply_threads * sizeof(ulonglong2));
+  g.apply_smem = (int)(kItemRecords * sizeof(ulonglong2) + (size_t)g.R * g.apply_threads * sizeof(ulonglong2));
   // the set-up sized the launch for the widest graph; a narrower one fits
   g.apply_grid = ds->apply_grid;
   g.prof_on = false;

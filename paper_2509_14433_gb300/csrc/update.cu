@@ -176,30 +176,48 @@ __device__ __forceinline__ uint64_t mix_tail(uint64_t z) {
   return z ^ (z >> 31);
 }
 
+// Row of an index from its hash: trailing zeros, capped at D-1. With
+// D <= 32 the low hash word decides (a zero low word means depth >= 32 >=
+// D-1); wider sketches fall back to the 64-bit count in that rare case.
+template <bool kWide>
+__device__ __forceinline__ uint32_t depth_fast(uint64_t h, uint32_t D) {
+  const uint32_t lo = (uint32_t)h;
+  uint32_t d = (uint32_t)__ffs(lo) - 1u;  // lo == 0 gives 0xFFFFFFFF
+  if (kWide && lo == 0) d = depth_of(h, D);
+  return min(d, D - 1);
+}
+
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 // Fold the records of one work item into the sketches of its vertex.
 // Thread layout: tid = r*P + s; r < L is the layer, s < C a column, s == C
 // the checksum lane, which owns the deterministic bucket (its row 0). A lane
 // is the only writer of its rows in shared memory, so no shared atomics are
-// needed, and every active lane runs the same instruction stream; the
-// checksum of a record reaches the column lanes by shuffle.
+// needed, and every lane runs the same branch-free instruction stream (lanes
+// past the layout fold into their own rows, which are never written back);
+// the checksum of a record reaches the column lanes by shuffle. Records are
+// hashed one group of four ahead of the group being folded, so the hashing
+// fills the latency of the fold's shared-memory read-modify-writes.
+template <bool kWide>
 __global__ void k_apply(ulonglong2* __restrict__ sketch, const uint64_t* __restrict__ keys,
                         const uint64_t* __restrict__ rec, const uint4* __restrict__ items, uint32_t* gc,
                         uint32_t V, uint32_t L, uint32_t C, uint32_t D, uint32_t W, uint32_t P, uint32_t R) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  uint64_t* s_rec = reinterpret_cast<uint64_t*>(smem_raw);
-  uint64_t* s_pre = s_rec + kItemRecords;
-  ulonglong2* s_acc = reinterpret_cast<ulonglong2*>(s_pre + kItemRecords);
+  ulonglong2* s_xp = reinterpret_cast<ulonglong2*>(smem_raw);  // {idx, pre(idx)}
+  ulonglong2* s_acc = s_xp + kItemRecords;
   __shared__ uint32_t s_item;
 
   if (ld_cg(&gc[GC_ERR]) & kErrInval) return;
   const uint32_t tid = threadIdx.x, lane = tid & 31;
   const uint32_t r = tid / P, s = tid % P;
   const bool active = r < L && s <= C;
-  const bool is_chk = s == C;
+  const bool row0 = !active || s == C;  // checksum lane and idle lanes use row 0 only
   const uint64_t kpre = active ? pre_mix(keys[r * (C + 1) + s]) : 0;
   const uint32_t chk_lane = (lane & ~(P - 1)) | C;
-  const uint32_t jbase = is_chk ? 0u : 1u + s * D;  // first bucket of this lane's column
-  const uint32_t nrows = is_chk ? 1u : R;
+  const uint32_t jbase = s == C ? 0u : 1u + s * D;  // first bucket of this lane's column
+  const uint32_t nrows = s == C ? 1u : R;
   // row d of this lane lives at s_acc[d * blockDim.x + tid]: the 8 lanes of a
   // shared-memory phase always hit 8 distinct 16-byte bank groups
   ulonglong2* my_rows = s_acc + tid;
@@ -215,59 +233,63 @@ __global__ void k_apply(ulonglong2* __restrict__ sketch, const uint64_t* __restr
     const uint4 item = items[it];
     const uint32_t w = item.x, beg = item.y, n = item.z - item.y;
     const bool excl = item.w != 0;
+    ulonglong2* gb = sketch + ((size_t)(r < L ? r : 0) * V + w) * W + jbase;
+    if (active) {  // bring this lane's buckets to L2 for the write-back
+      prefetch_l2(gb);
+      if (nrows > 1) {
+        prefetch_l2(gb + 6);
+        prefetch_l2(gb + nrows - 1);
+      }
+    }
     for (uint32_t i = tid; i < n; i += blockDim.x) {
       const uint64_t x = rec[beg + i];
-      s_rec[i] = x;
-      s_pre[i] = pre_mix(x);
+      s_xp[i] = make_ulonglong2(x, pre_mix(x));
     }
     __syncthreads();
 
-    ulonglong2* gb = sketch + ((size_t)(r < L ? r : 0) * V + w) * W + jbase;
-    uint32_t i = 0;
-    // four records per step: four independent hash chains per lane
-    for (; i + 4 <= n; i += 4) {
-      uint64_t x[4], h[4], gm[4];
+    auto fold = [&](uint64_t x, uint64_t h, uint64_t g) {
+      uint32_t d = depth_fast<kWide>(h, D);
+      if (row0) d = 0;
+      if (d < R) {
+        ulonglong2 v = my_rows[d * rs];
+        v.x ^= x;
+        v.y ^= g;
+        my_rows[d * rs] = v;
+      } else {
+        xor_bucket_atomic(gb + d, make_ulonglong2(x, g));
+      }
+    };
+
+    const uint32_t nfull = n >> 2;
+    ulonglong2 xc[4];
+    uint64_t hc[4];
 #pragma unroll
-      for (int k = 0; k < 4; k++) {
-        x[k] = s_rec[i + k];
-        h[k] = mix_tail(s_pre[i + k] ^ kpre);
+    for (uint32_t k = 0; k < 4; k++) {
+      xc[k] = s_xp[min(k, n - 1)];
+      hc[k] = mix_tail(xc[k].y ^ kpre);
+    }
+    for (uint32_t g = 0; g < nfull; g++) {
+      uint64_t gm[4], hn[4];
+      ulonglong2 xn[4];
+#pragma unroll
+      for (uint32_t k = 0; k < 4; k++) gm[k] = __shfl_sync(0xffffffffu, hc[k], chk_lane);
+#pragma unroll
+      for (uint32_t k = 0; k < 4; k++) {  // next group (clamped: the last one is recomputed harmlessly)
+        xn[k] = s_xp[min(4 * g + 4 + k, n - 1)];
+        hn[k] = mix_tail(xn[k].y ^ kpre);
       }
 #pragma unroll
-      for (int k = 0; k < 4; k++) gm[k] = __shfl_sync(0xffffffffu, h[k], chk_lane);
+      for (uint32_t k = 0; k < 4; k++) fold(xc[k].x, hc[k], gm[k]);
 #pragma unroll
-      for (int k = 0; k < 4; k++) {
-        const uint32_t lo = (uint32_t)h[k];
-        uint32_t d = (uint32_t)__ffs(lo) - 1;
-        if (lo == 0) d = depth_of(h[k], D);
-        d = min(d, D - 1);
-        if (is_chk) d = 0;
-        if (active) {
-          if (d < R) {
-            ulonglong2 v = my_rows[d * rs];
-            v.x ^= x[k];
-            v.y ^= gm[k];
-            my_rows[d * rs] = v;
-          } else {
-            xor_bucket_atomic(gb + d, make_ulonglong2(x[k], gm[k]));
-          }
-        }
+      for (uint32_t k = 0; k < 4; k++) {
+        xc[k] = xn[k];
+        hc[k] = hn[k];
       }
     }
-    for (; i < n; i++) {
-      const uint64_t x = s_rec[i];
-      const uint64_t h = mix_tail(s_pre[i] ^ kpre);
-      const uint64_t gm = __shfl_sync(0xffffffffu, h, chk_lane);
-      uint32_t d = is_chk ? 0u : depth_of(h, D);
-      if (active) {
-        if (d < R) {
-          ulonglong2 v = my_rows[d * rs];
-          v.x ^= x;
-          v.y ^= gm;
-          my_rows[d * rs] = v;
-        } else {
-          xor_bucket_atomic(gb + d, make_ulonglong2(x, gm));
-        }
-      }
+    for (uint32_t i = 4 * nfull; i < n; i++) {
+      const ulonglong2 x = s_xp[i];
+      const uint64_t h = mix_tail(x.y ^ kpre);
+      fold(x.x, h, __shfl_sync(0xffffffffu, h, chk_lane));
     }
 
     // write back only the touched (non-zero) rows of this vertex
@@ -298,6 +320,8 @@ __global__ void k_apply(ulonglong2* __restrict__ sketch, const uint64_t* __restr
             if (nz[q]) xor_bucket_atomic(gb + d0 + q, v[q]);
         }
       }
+    } else {
+      for (uint32_t d = 0; d < R; d++) my_rows[d * rs] = make_ulonglong2(0, 0);
     }
     __syncthreads();
   }
@@ -307,11 +331,16 @@ __global__ void k_apply(ulonglong2* __restrict__ sketch, const uint64_t* __restr
 // raise it, so that a graph created later never shrinks it below what an
 // earlier graph's launches need.
 cudaError_t raise_apply_smem_limit(int bytes) {
-  cudaFuncAttributes fa;
-  cudaError_t e = cudaFuncGetAttributes(&fa, k_apply);
-  if (e != cudaSuccess) return e;
-  if (fa.maxDynamicSharedSizeBytes >= bytes) return cudaSuccess;
-  return cudaFuncSetAttribute(k_apply, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  const void* fns[2] = {(const void*)k_apply<false>, (const void*)k_apply<true>};
+  for (const void* f : fns) {
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, f);
+    if (e != cudaSuccess) return e;
+    if (fa.maxDynamicSharedSizeBytes >= bytes) continue;
+    e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 cudaError_t setup_update(cupc_graph* g) {
@@ -319,11 +348,12 @@ cudaError_t setup_update(cupc_graph* g) {
   while (g->P < g->C + 1) g->P <<= 1;
   g->R = g->D < kSmemRows ? g->D : kSmemRows;
   g->apply_threads = (int)(((g->L * g->P) + 31) / 32 * 32);
-  g->apply_smem = (int)(2 * kItemRecords * sizeof(uint64_t) + (size_t)g->R * g->apply_threads * sizeof(ulonglong2));
+  g->apply_smem = (int)(kItemRecords * sizeof(ulonglong2) + (size_t)g->R * g->apply_threads * sizeof(ulonglong2));
   cudaError_t e = raise_apply_smem_limit(g->apply_smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_apply, g->apply_threads, g->apply_smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, g->D > 32 ? k_apply<true> : k_apply<false>,
+                                                    g->apply_threads, g->apply_smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   g->apply_grid = per_sm * g->sms;
@@ -341,8 +371,9 @@ cudaError_t launch_update_chunk(cupc_graph* g, const uint32_t* edges, size_t n, 
   }
   ProfScope ps(g, s, PC_APPLY, 1);
   int agrid = (int)std::min<size_t>((size_t)g->apply_grid, 2 * n);
-  k_apply<<<agrid, g->apply_threads, g->apply_smem, s>>>(g->sketch, g->keys, g->rec, g->items, g->gc, g->V, g->L,
-                                                          g->C, g->D, g->W, g->P, g->R);
+  auto kern = g->D > 32 ? k_apply<true> : k_apply<false>;
+  kern<<<agrid, g->apply_threads, g->apply_smem, s>>>(g->sketch, g->keys, g->rec, g->items, g->gc, g->V, g->L, g->C,
+                                                       g->D, g->W, g->P, g->R);
   return cudaGetLastError();
 }
 
