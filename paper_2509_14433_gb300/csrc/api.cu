@@ -51,7 +51,7 @@ Dims derive(uint32_t V, const cupc_params* p) {
 // Byte offsets of every device array inside the workspace.
 struct Layout {
   size_t sketch, keys, gc, cnt, cursor, rec, items, stage_edges, stage_ops, label, parent, minv, rcnt, roff,
-      perm, tgt, plist, tilesum, final_, merged, partial, best, cand, forest, forest_sorted, acc, log_ids, log_live,
+      perm, pcount, final_, merged, best, best2, cand, forest, forest_sorted, acc, log_ids, log_live,
       log_ncand, total;
 };
 
@@ -80,13 +80,11 @@ Layout layout(const Dims& d) {
   l.rcnt = take(V * 4);
   l.roff = take(V * 4);
   l.perm = take(V * 4);
-  l.tgt = take(V * 4);
-  l.plist = take(V * 4);
-  l.tilesum = take((V / 2048 + 2) * 4);
+  l.pcount = take(V * 4);
   l.final_ = take(V);
   l.merged = take(V);
-  l.partial = take(V);
   l.best = take(V * 8);
+  l.best2 = take(V * 8);
   l.cand = take(V * 8);
   l.forest = take(V * 8);
   l.forest_sorted = take(V * 8);
@@ -193,13 +191,11 @@ cupc_status cupc_init(uint32_t V, uint64_t seed, const cupc_params* params, void
   g->rcnt = (uint32_t*)(b + l.rcnt);
   g->roff = (uint32_t*)(b + l.roff);
   g->perm = (uint32_t*)(b + l.perm);
-  g->tgt = (uint32_t*)(b + l.tgt);
-  g->plist = (uint32_t*)(b + l.plist);
-  g->tilesum = (uint32_t*)(b + l.tilesum);
+  g->pcount = (uint32_t*)(b + l.pcount);
   g->final_ = (uint8_t*)(b + l.final_);
   g->merged = (uint8_t*)(b + l.merged);
-  g->partial = (uint8_t*)(b + l.partial);
   g->best = (uint64_t*)(b + l.best);
+  g->best2 = (uint64_t*)(b + l.best2);
   g->cand = (uint64_t*)(b + l.cand);
   g->forest = (uint64_t*)(b + l.forest);
   g->forest_sorted = (uint64_t*)(b + l.forest_sorted);

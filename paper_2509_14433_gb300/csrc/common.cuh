@@ -41,16 +41,15 @@ enum : uint32_t {
   GC_NEXT_ITEM = 2,  // dynamic scheduler cursor of the apply kernel
   GC_NFOREST = 3,
   GC_NZ = 4,         // non-ZERO samples this round
-  GC_ACTIVE = 5,     // MSF: candidates still crossing components
+  GC_ACTIVE = 5,     // MSF: candidates still crossing components (even iterations)
   GC_NMEMBERS = 6,   // live members this round
   GC_NFAIL = 7,
   GC_NFP = 8,
   GC_ROUNDS = 9,
   GC_COMPLETE = 10,
   GC_LOGLEN = 11,
-  GC_NPARTIAL = 12,
+  GC_ACTIVE_ODD = 12,  // MSF: same flag for odd iterations
   GC_BAR_COUNT = 13,
-  GC_BAR_GEN = 14,
   GC_RECOVERIES = 15,
   GC_BATCHES = 16,   // update chunks applied
   GC_SLOTS = 32
@@ -118,13 +117,11 @@ struct cupc_graph {
   uint32_t* rcnt;    // V
   uint32_t* roff;    // V
   uint32_t* perm;    // V
-  uint32_t* tgt;     // V
-  uint32_t* plist;   // V
-  uint32_t* tilesum; // V/2048 + 1
+  uint32_t* pcount;  // V: spans of a component reduced so far
   uint8_t* final_;   // V
   uint8_t* merged;   // V
-  uint8_t* partial;  // V
   uint64_t* best;    // V
+  uint64_t* best2;   // V
   uint64_t* cand;    // V
   uint64_t* forest;  // V
   uint64_t* forest_sorted;  // V

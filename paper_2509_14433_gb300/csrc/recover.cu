@@ -21,8 +21,6 @@
 //   relabel     every vertex takes the minimum vertex id of its component
 // A component whose merged sketch is ZERO has an empty cut; it is not sampled
 // again until it changes.
-#include <cooperative_groups.h>
-
 #include "common.cuh"
 
 namespace cupc {
@@ -31,42 +29,42 @@ struct RecArgs {
   const ulonglong2* sketch;
   const uint64_t* keys;
   uint32_t V, L, C, D, W;
-  uint32_t *label, *parent, *minv, *rcnt, *roff, *perm, *tgt, *plist, *tilesum;
-  uint8_t *final_, *merged, *partial;
-  uint64_t *best, *cand, *forest, *log_ids;
+  uint32_t *label, *parent, *minv, *rcnt, *roff, *perm, *pcount;
+  uint8_t *final_, *merged;
+  uint64_t *best0, *best1, *cand, *forest, *log_ids;
   ulonglong2* acc;
   uint32_t *log_live, *log_ncand;
   uint32_t* gc;
 };
 
-// Grid barrier for a cooperative launch. The wait is bounded: after
-// kWaitLimitNs it records kErrTimeout and returns false in every thread of
-// the CTA, which must then return.
-__device__ __forceinline__ bool grid_barrier(uint32_t* gc, uint32_t nblocks, int* s_ok) {
+// Grid barrier for a cooperative launch: CTA thread 0 adds one to an arrival
+// counter that only grows during the launch (the host zeroes it before) and
+// waits until all CTAs of this barrier have arrived. The wait is bounded:
+// after kWaitLimitNs it records kErrTimeout and returns false in every
+// thread of the CTA, which must then return.
+__device__ __forceinline__ bool grid_barrier(uint32_t* gc, uint32_t nblocks, uint32_t& epoch, int* s_ok) {
   __syncthreads();
   if (threadIdx.x == 0) {
-    volatile uint32_t* gen = gc + GC_BAR_GEN;
-    const uint32_t my_gen = *gen;
+    epoch += 1;
+    const uint32_t target = epoch * nblocks;
     int ok = 1;
     __threadfence();
-    const uint32_t arrived = atomicAdd(&gc[GC_BAR_COUNT], 1u);
-    if (arrived == nblocks - 1) {
-      atomicExch(&gc[GC_BAR_COUNT], 0u);
-      __threadfence();
-      atomicAdd(&gc[GC_BAR_GEN], 1u);
-    } else {
-      const uint64_t t0 = global_timer_ns();
-      while (*gen == my_gen) {
+    atomicAdd(&gc[GC_BAR_COUNT], 1u);
+    volatile uint32_t* cnt = gc + GC_BAR_COUNT;
+    uint64_t t0 = 0;
+    for (uint32_t spin = 0; *cnt < target; spin++) {
+      if ((spin & 63) == 63) {
+        const uint64_t t = global_timer_ns();
+        if (t0 == 0) t0 = t;
         if (ld_cg(&gc[GC_ERR]) & kErrTimeout) {
           ok = 0;
           break;
         }
-        if (global_timer_ns() - t0 > kWaitLimitNs) {
+        if (t - t0 > kWaitLimitNs) {
           atomicOr(&gc[GC_ERR], kErrTimeout);
           ok = 0;
           break;
         }
-        __nanosleep(32);
       }
     }
     __threadfence();
@@ -76,13 +74,18 @@ __device__ __forceinline__ bool grid_barrier(uint32_t* gc, uint32_t nblocks, int
   return *s_ok != 0;
 }
 
-__device__ __forceinline__ uint32_t find_root(const uint32_t* parent, uint32_t x, uint32_t V) {
+// Root of x in the hook forest; points x straight at it. Other threads may
+// rewrite parent[] concurrently, but only ever to an ancestor, so every value
+// read is an ancestor and the walk ends at the same root.
+__device__ __forceinline__ uint32_t find_root(uint32_t* parent, uint32_t x, uint32_t V) {
+  uint32_t r = x;
   for (uint32_t k = 0; k < V; k++) {
-    uint32_t p = ld_cg(&parent[x]);
-    if (p == x) break;
-    x = p;
+    const uint32_t p = ld_cg(&parent[r]);
+    if (p == r) break;
+    r = p;
   }
-  return x;
+  if (r != x && ld_cg(&parent[x]) != r) parent[x] = r;
+  return r;
 }
 
 // Sample a layer-r sum held by a warp (lane l holds buckets l + 32q): ZERO
@@ -148,12 +151,15 @@ __device__ __forceinline__ void warp_xor_row(ulonglong2 (&acc)[kWarpBuckets], co
   }
 }
 
-__global__ void __launch_bounds__(kRecThreads) k_recover(RecArgs a) {
+__global__ void __launch_bounds__(kRecThreads, 1) k_recover(RecArgs a) {
   __shared__ int s_ok;
   const uint32_t V = a.V, W = a.W, nb = gridDim.x, tid = threadIdx.x, lane = tid & 31;
   const uint32_t gtid = blockIdx.x * blockDim.x + tid, gstride = gridDim.x * blockDim.x;
   const uint32_t wpb = blockDim.x >> 5, gwarp = blockIdx.x * wpb + (tid >> 5), nwarps = gridDim.x * wpb;
   uint32_t* gc = a.gc;
+  uint32_t epoch = 0;
+#define CUPC_GRID_SYNC() \
+  if (!grid_barrier(gc, nb, epoch, &s_ok)) return
 
   for (uint32_t w = gtid; w < V; w += gstride) {
     a.label[w] = w;
@@ -162,8 +168,8 @@ __global__ void __launch_bounds__(kRecThreads) k_recover(RecArgs a) {
     a.minv[w] = kNoneU32;
     a.merged[w] = 0;
     a.cand[w] = kNone;
-    a.best[w] = kNone;
-    a.tgt[w] = kNoneU32;
+    a.best0[w] = kNone;
+    a.best1[w] = kNone;
     a.rcnt[w] = 0;
   }
   if (gtid == 0) {
@@ -175,7 +181,7 @@ __global__ void __launch_bounds__(kRecThreads) k_recover(RecArgs a) {
     gc[GC_ROUNDS] = 0;
     gc[GC_NZ] = 0;
     gc[GC_ACTIVE] = 0;
-    gc[GC_NPARTIAL] = 0;
+    gc[GC_ACTIVE_ODD] = 0;
     gc[GC_NMEMBERS] = 0;
     gc[GC_RECOVERIES] += 1;
   }
@@ -183,22 +189,15 @@ __global__ void __launch_bounds__(kRecThreads) k_recover(RecArgs a) {
     a.log_live[r] = 0;
     a.log_ncand[r] = 0;
   }
-  if (!grid_barrier(gc, nb, &s_ok)) return;
+  CUPC_GRID_SYNC();
 
   for (uint32_t r = 0; r < a.L; r++) {
     const uint64_t kchk = a.keys[r * (a.C + 1) + a.C];
-    // ---- group live vertices by component (rounds >= 1): count, allocate a
-    // segment per component, scatter
+    // ---- group the live vertices of round r by component: the relabel of
+    // round r-1 counted them; give each component a segment (warp-aggregated
+    // atomics), then scatter
     uint32_t nmem = V;
     if (r > 0) {
-      for (uint32_t w = gtid; w < V; w += gstride) {
-        a.parent[w] = w;
-        a.minv[w] = kNoneU32;
-        a.merged[w] = 0;
-        const uint32_t K = ld_cg(&a.label[w]);
-        if (!ld_cg(&a.final_[K])) atomicAdd(&a.rcnt[K], 1u);
-      }
-      if (!grid_barrier(gc, nb, &s_ok)) return;
       for (uint32_t base = blockIdx.x * blockDim.x; base < V; base += gstride) {
         const uint32_t K = base + tid;
         const uint32_t c = K < V ? ld_cg(&a.rcnt[K]) : 0;
@@ -216,18 +215,24 @@ __global__ void __launch_bounds__(kRecThreads) k_recover(RecArgs a) {
           a.roff[K] = wbase + inc - c;
           a.rcnt[K] = wbase + inc - c;  // scatter cursor, then the segment end
         }
+        if (K < V) {
+          a.parent[K] = K;
+          a.minv[K] = kNoneU32;
+          a.merged[K] = 0;
+        }
       }
-      if (!grid_barrier(gc, nb, &s_ok)) return;
+      CUPC_GRID_SYNC();
       for (uint32_t w = gtid; w < V; w += gstride) {
         const uint32_t K = ld_cg(&a.label[w]);
         if (!ld_cg(&a.final_[K])) a.perm[atomicAdd(&a.rcnt[K], 1u)] = w;
       }
-      if (!grid_barrier(gc, nb, &s_ok)) return;
+      CUPC_GRID_SYNC();
       nmem = ld_cg(&gc[GC_NMEMBERS]);
     }
 
-    // ---- reduce + sample, one warp per span of members; round 0 has one
-    // vertex per span (every vertex is its own component)
+    // ---- reduce + sample, one warp per span of members (round 0: one
+    // vertex per span, every vertex is its own component). A component over
+    // several spans is XORed into acc[K]; the last span to finish samples it.
     const uint32_t span = r == 0 ? 1u : kRecSpan;
     const uint32_t nspans = (nmem + span - 1) / span;
     for (uint32_t sp = gwarp; sp < nspans; sp += nwarps) {
@@ -249,12 +254,13 @@ __global__ void __launch_bounds__(kRecThreads) k_recover(RecArgs a) {
           const uint32_t w = __shfl_sync(0xffffffffu, mw, m);
           warp_xor_row(acc, a.sketch + ((size_t)r * V + w) * W, W, lane);
         }
-        const bool whole = r == 0 || (ld_cg(&a.roff[K]) == i0 + i && ld_cg(&a.rcnt[K]) == i0 + j);
-        if (whole) {
-          uint64_t e = 0;
-          const uint32_t res = warp_sample(acc, W, V, kchk, e);
-          if (lane == 0) take_sample(a, r, K, res, e);
-        } else {
+        uint32_t nsp = 1;
+        if (r > 0) {
+          const uint32_t s0 = ld_cg(&a.roff[K]), s1 = ld_cg(&a.rcnt[K]);
+          nsp = (s1 - 1) / span - s0 / span + 1;
+        }
+        bool mine = true;
+        if (nsp > 1) {
           ulonglong2* dst = a.acc + (size_t)K * W;
 #pragma unroll
           for (uint32_t q = 0; q < kWarpBuckets; q++) {
@@ -264,108 +270,109 @@ __global__ void __launch_bounds__(kRecThreads) k_recover(RecArgs a) {
               atomicXor(&dst[b].y, acc[q].y);
             }
           }
-          // the span holding the component's first member lists it once
-          if (lane == 0 && ld_cg(&a.roff[K]) == i0 + i) a.plist[atomicAdd(&gc[GC_NPARTIAL], 1u)] = K;
+          __threadfence();
+          uint32_t prev = 0;
+          if (lane == 0) prev = atomicAdd(&a.pcount[K], 1u);
+          mine = __shfl_sync(0xffffffffu, prev, 0) + 1 == nsp;
+          if (mine) {  // the last span: every other span's XOR is in acc[K]
+            __threadfence();
+#pragma unroll
+            for (uint32_t q = 0; q < kWarpBuckets; q++) {
+              const uint32_t b = lane + 32 * q;
+              acc[q] = make_ulonglong2(0, 0);
+              if (b < W) {
+                acc[q] = __ldcg(dst + b);
+                dst[b] = make_ulonglong2(0, 0);
+              }
+            }
+            if (lane == 0) a.pcount[K] = 0;
+          }
+        }
+        if (mine) {
+          uint64_t e = 0;
+          const uint32_t res = warp_sample(acc, W, V, kchk, e);
+          if (lane == 0) take_sample(a, r, K, res, e);
         }
         i = j;
       }
     }
-    if (!grid_barrier(gc, nb, &s_ok)) return;
-
-    // ---- sample components spread over several spans, one warp each
-    const uint32_t npart = ld_cg(&gc[GC_NPARTIAL]);
-    for (uint32_t p = gwarp; p < npart; p += nwarps) {
-      const uint32_t K = ld_cg(&a.plist[p]);
-      ulonglong2* src = a.acc + (size_t)K * W;
-      ulonglong2 acc[kWarpBuckets];
-#pragma unroll
-      for (uint32_t q = 0; q < kWarpBuckets; q++) {
-        const uint32_t b = lane + 32 * q;
-        acc[q] = make_ulonglong2(0, 0);
-        if (b < W) {
-          acc[q] = __ldcg(src + b);
-          src[b] = make_ulonglong2(0, 0);
-        }
-      }
-      uint64_t e = 0;
-      const uint32_t res = warp_sample(acc, W, V, kchk, e);
-      if (lane == 0) take_sample(a, r, K, res, e);
-    }
-    if (!grid_barrier(gc, nb, &s_ok)) return;
+    CUPC_GRID_SYNC();
     if (gtid == 0) gc[GC_ROUNDS] = r + 1;
     if (ld_cg(&gc[GC_NZ]) == 0) {
       if (gtid == 0) gc[GC_COMPLETE] = 1;
       break;
     }
 
-    // ---- hook: minimum spanning forest of the candidates (Boruvka)
+    // ---- hook: minimum spanning forest of the candidates by Boruvka. A
+    // root's key is edge*V + (root on the other side), so the min key names
+    // the min-id crossing edge and where it leads; two roots that chose the
+    // same edge hook once (the larger id under the smaller).
     for (uint32_t iter = 0; iter < 64; iter++) {
+      uint64_t* bc = (iter & 1) ? a.best1 : a.best0;
+      uint64_t* bn = (iter & 1) ? a.best0 : a.best1;
+      const uint32_t act = (iter & 1) ? GC_ACTIVE_ODD : GC_ACTIVE, act_next = (iter & 1) ? GC_ACTIVE : GC_ACTIVE_ODD;
       for (uint32_t K = gtid; K < V; K += gstride) {
         const uint64_t e = ld_cg(&a.cand[K]);
         if (e == kNone) continue;
         const uint32_t ra = find_root(a.parent, ld_cg(&a.label[(uint32_t)(e / V)]), V);
         const uint32_t rb = find_root(a.parent, ld_cg(&a.label[(uint32_t)(e % V)]), V);
         if (ra != rb) {
-          atomicMin((unsigned long long*)&a.best[ra], (unsigned long long)e);
-          atomicMin((unsigned long long*)&a.best[rb], (unsigned long long)e);
-          if (ld_cg(&gc[GC_ACTIVE]) == 0) atomicExch(&gc[GC_ACTIVE], 1u);
+          atomicMin((unsigned long long*)&bc[ra], (unsigned long long)(e * V + rb));
+          atomicMin((unsigned long long*)&bc[rb], (unsigned long long)(e * V + ra));
+          if (ld_cg(&gc[act]) == 0) atomicExch(&gc[act], 1u);
         }
       }
-      if (!grid_barrier(gc, nb, &s_ok)) return;
-      if (ld_cg(&gc[GC_ACTIVE]) == 0) break;
+      CUPC_GRID_SYNC();
+      if (ld_cg(&gc[act]) == 0) break;
       for (uint32_t x = gtid; x < V; x += gstride) {
-        const uint64_t e = ld_cg(&a.best[x]);
-        if (e == kNone) continue;
-        const uint32_t ra = find_root(a.parent, ld_cg(&a.label[(uint32_t)(e / V)]), V);
-        const uint32_t rb = find_root(a.parent, ld_cg(&a.label[(uint32_t)(e % V)]), V);
-        a.tgt[x] = ra == x ? rb : ra;
-      }
-      if (!grid_barrier(gc, nb, &s_ok)) return;
-      for (uint32_t x = gtid; x < V; x += gstride) {
-        const uint32_t o = ld_cg(&a.tgt[x]);
-        if (o == kNoneU32) continue;
-        const bool mutual = ld_cg(&a.tgt[o]) == x;
+        bn[x] = kNone;
+        const uint64_t key = ld_cg(&bc[x]);
+        if (key == kNone) continue;
+        const uint64_t e = key / V;
+        const uint32_t o = (uint32_t)(key % V);
+        const bool mutual = ld_cg(&bc[o]) / V == e;
         if (!mutual || x > o) {
           a.parent[x] = o;
-          a.forest[atomicAdd(&gc[GC_NFOREST], 1u)] = ld_cg(&a.best[x]);
+          a.forest[atomicAdd(&gc[GC_NFOREST], 1u)] = e;
         }
       }
-      if (!grid_barrier(gc, nb, &s_ok)) return;
-      for (uint32_t x = gtid; x < V; x += gstride) {
-        const uint32_t p = ld_cg(&a.parent[x]);
-        if (p != x) a.parent[x] = find_root(a.parent, p, V);
-        a.best[x] = kNone;
-        a.tgt[x] = kNoneU32;
-      }
-      if (gtid == 0) gc[GC_ACTIVE] = 0;
-      if (!grid_barrier(gc, nb, &s_ok)) return;
+      if (gtid == 0) gc[act_next] = 0;
+      CUPC_GRID_SYNC();
     }
 
     // ---- relabel to the minimum vertex id of each component; clear the
-    // round's scratch for the next round
+    // round's scratch
     for (uint32_t w = gtid; w < V; w += gstride) {
       a.rcnt[w] = 0;
       a.cand[w] = kNone;
+      a.best0[w] = kNone;
+      a.best1[w] = kNone;
       if (ld_cg(&a.label[w]) != w) continue;
-      const uint32_t root = ld_cg(&a.parent[w]);
+      const uint32_t root = find_root(a.parent, w, V);
       atomicMin(&a.minv[root], w);
       if (root != w) a.merged[root] = 1;
     }
     if (gtid == 0) {
       gc[GC_NZ] = 0;
-      gc[GC_NPARTIAL] = 0;
       gc[GC_NMEMBERS] = 0;
+      gc[GC_ACTIVE] = 0;
+      gc[GC_ACTIVE_ODD] = 0;
     }
-    if (!grid_barrier(gc, nb, &s_ok)) return;
+    CUPC_GRID_SYNC();
+    // new labels; the members of next round's live components are counted
+    // here (a merged component is live; an unmerged one keeps its flag)
     for (uint32_t w = gtid; w < V; w += gstride) {
       const uint32_t K = ld_cg(&a.label[w]);
-      const uint32_t root = ld_cg(&a.parent[K]);
+      const uint32_t root = find_root(a.parent, K, V);
       const uint32_t nl = ld_cg(&a.minv[root]);
+      const bool mg = ld_cg(&a.merged[root]) != 0;
       a.label[w] = nl;
-      if (w == root && ld_cg(&a.merged[root])) a.final_[nl] = 0;
+      if (w == root && mg) a.final_[nl] = 0;
+      if (mg || !ld_cg(&a.final_[root])) atomicAdd(&a.rcnt[nl], 1u);
     }
-    if (!grid_barrier(gc, nb, &s_ok)) return;
+    CUPC_GRID_SYNC();
   }
+#undef CUPC_GRID_SYNC
 }
 
 cudaError_t setup_recover(cupc_graph* g) {
@@ -398,13 +405,11 @@ cudaError_t launch_recover(cupc_graph* g, cudaStream_t s) {
   a.rcnt = g->rcnt;
   a.roff = g->roff;
   a.perm = g->perm;
-  a.tgt = g->tgt;
-  a.plist = g->plist;
-  a.tilesum = g->tilesum;
+  a.pcount = g->pcount;
   a.final_ = g->final_;
   a.merged = g->merged;
-  a.partial = g->partial;
-  a.best = g->best;
+  a.best0 = g->best;
+  a.best1 = g->best2;
   a.cand = g->cand;
   a.forest = g->forest;
   a.log_ids = g->log_ids;
