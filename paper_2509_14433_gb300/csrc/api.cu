@@ -85,7 +85,7 @@ Layout layout(const Dims& d) {
   l.merged = take(V);
   l.best = take(V * 8);
   l.best2 = take(V * 8);
-  l.cand = take(V * 8);
+  l.cand = take(V * 16);
   l.forest = take(V * 8);
   l.forest_sorted = take(V * 8);
   l.acc = take(V * d.W * sizeof(ulonglong2));
@@ -196,7 +196,7 @@ cupc_status cupc_init(uint32_t V, uint64_t seed, const cupc_params* params, void
   g->merged = (uint8_t*)(b + l.merged);
   g->best = (uint64_t*)(b + l.best);
   g->best2 = (uint64_t*)(b + l.best2);
-  g->cand = (uint64_t*)(b + l.cand);
+  g->cand = (ulonglong2*)(b + l.cand);
   g->forest = (uint64_t*)(b + l.forest);
   g->forest_sorted = (uint64_t*)(b + l.forest_sorted);
   g->acc = (ulonglong2*)(b + l.acc);

@@ -122,7 +122,7 @@ struct cupc_graph {
   uint8_t* merged;   // V
   uint64_t* best;    // V
   uint64_t* best2;   // V
-  uint64_t* cand;    // V
+  ulonglong2* cand;  // V: {candidate edge, endpoint labels}
   uint64_t* forest;  // V
   uint64_t* forest_sorted;  // V
   ulonglong2* acc;   // V*W (partial component sums)

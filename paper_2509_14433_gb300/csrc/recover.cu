@@ -31,7 +31,8 @@ struct RecArgs {
   uint32_t V, L, C, D, W;
   uint32_t *label, *parent, *minv, *rcnt, *roff, *perm, *pcount;
   uint8_t *final_, *merged;
-  uint64_t *best0, *best1, *cand, *forest, *log_ids;
+  uint64_t *best0, *best1, *forest, *log_ids;
+  ulonglong2* cand;  // {edge, label[u] << 32 | label[v]} of a component's candidate
   ulonglong2* acc;
   uint32_t *log_live, *log_ncand;
   uint32_t* gc;
@@ -115,27 +116,63 @@ __device__ __forceinline__ uint32_t warp_sample(const ulonglong2 (&acc)[kWarpBuc
   return found ? 1u : 2u;
 }
 
-// Record the sample of component K (one lane).
-__device__ __forceinline__ void take_sample(const RecArgs& a, uint32_t r, uint32_t K, uint32_t res, uint64_t e) {
-  atomicAdd(&a.log_live[r], 1u);
-  if (res == 0) {
-    a.final_[K] = 1;
-    return;
+// Book the samples stashed in a warp, one per lane (K = kNoneU32: none):
+// ZERO marks the component final; GOOD with an edge that leaves K becomes
+// its candidate (stored with both endpoint labels) and is logged; GOOD with
+// an edge inside K is a checksum false positive. Counters are aggregated per
+// warp. Every lane of the warp must call this.
+__device__ __forceinline__ void book_samples(const RecArgs& a, uint32_t r, uint32_t K, uint32_t res, uint64_t e) {
+  const uint32_t lane = threadIdx.x & 31;
+  const bool have = K != kNoneU32;
+  bool cand = false;
+  if (have) {
+    if (res == 0) {
+      a.final_[K] = 1;
+    } else if (res == 1) {
+      const uint32_t u = (uint32_t)(e / a.V), v = (uint32_t)(e % a.V);
+      const uint32_t lu = r ? ld_cg(&a.label[u]) : u, lv = r ? ld_cg(&a.label[v]) : v;
+      if ((lu == K) != (lv == K)) {
+        cand = true;
+        a.cand[K] = make_ulonglong2(e, ((uint64_t)lu << 32) | lv);
+      }
+    }
   }
-  atomicAdd(&a.gc[GC_NZ], 1u);
-  if (res == 2) {
-    atomicAdd(&a.gc[GC_NFAIL], 1u);
-    return;
+  const uint32_t m_have = __ballot_sync(0xffffffffu, have);
+  const uint32_t m_nz = __ballot_sync(0xffffffffu, have && res != 0);
+  const uint32_t m_fail = __ballot_sync(0xffffffffu, have && res == 2);
+  const uint32_t m_cand = __ballot_sync(0xffffffffu, cand);
+  const uint32_t m_fp = m_nz & ~m_fail & ~m_cand;
+  uint32_t base = 0;
+  if (lane == 0) {
+    if (m_have) atomicAdd(&a.log_live[r], (uint32_t)__popc(m_have));
+    if (m_nz) atomicAdd(&a.gc[GC_NZ], (uint32_t)__popc(m_nz));
+    if (m_fail) atomicAdd(&a.gc[GC_NFAIL], (uint32_t)__popc(m_fail));
+    if (m_fp) atomicAdd(&a.gc[GC_NFP], (uint32_t)__popc(m_fp));
+    if (m_cand) {
+      base = atomicAdd(&a.gc[GC_LOGLEN], (uint32_t)__popc(m_cand));
+      atomicAdd(&a.log_ncand[r], (uint32_t)__popc(m_cand));
+    }
   }
-  const uint32_t u = (uint32_t)(e / a.V), v = (uint32_t)(e % a.V);
-  const bool in_u = ld_cg(&a.label[u]) == K, in_v = ld_cg(&a.label[v]) == K;
-  if (in_u != in_v) {
-    a.cand[K] = e;
-    a.log_ids[atomicAdd(&a.gc[GC_LOGLEN], 1u)] = e;
-    atomicAdd(&a.log_ncand[r], 1u);
-  } else {
-    atomicAdd(&a.gc[GC_NFP], 1u);
+  base = __shfl_sync(0xffffffffu, base, 0);
+  if (cand) a.log_ids[base + __popc(m_cand & ((1u << lane) - 1))] = e;
+}
+
+// Position of this lane's item in ctr[key]'s range: lanes of the warp with
+// the same key share one atomicAdd. All 32 lanes call it; `take` selects the
+// lanes that add one item.
+__device__ __forceinline__ uint32_t warp_grab(uint32_t* ctr, uint32_t key, bool take) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t act = __ballot_sync(0xffffffffu, take);
+  uint32_t pos = 0;
+  if (take) {
+    const uint32_t peers = __match_any_sync(act, key);
+    const uint32_t leader = __ffs(peers) - 1;
+    uint32_t base = 0;
+    if (lane == leader) base = atomicAdd(&ctr[key], (uint32_t)__popc(peers));
+    base = __shfl_sync(peers, base, leader);
+    pos = base + __popc(peers & ((1u << lane) - 1));
   }
+  return pos;
 }
 
 __device__ __forceinline__ void warp_xor_row(ulonglong2 (&acc)[kWarpBuckets], const ulonglong2* __restrict__ row,
@@ -151,7 +188,7 @@ __device__ __forceinline__ void warp_xor_row(ulonglong2 (&acc)[kWarpBuckets], co
   }
 }
 
-__global__ void __launch_bounds__(kRecThreads, 1) k_recover(RecArgs a) {
+__global__ void __launch_bounds__(kRecThreads, 2) k_recover(RecArgs a) {
   __shared__ int s_ok;
   const uint32_t V = a.V, W = a.W, nb = gridDim.x, tid = threadIdx.x, lane = tid & 31;
   const uint32_t gtid = blockIdx.x * blockDim.x + tid, gstride = gridDim.x * blockDim.x;
@@ -167,7 +204,7 @@ __global__ void __launch_bounds__(kRecThreads, 1) k_recover(RecArgs a) {
     a.parent[w] = w;
     a.minv[w] = kNoneU32;
     a.merged[w] = 0;
-    a.cand[w] = kNone;
+    a.cand[w] = make_ulonglong2(kNone, 0);
     a.best0[w] = kNone;
     a.best1[w] = kNone;
     a.rcnt[w] = 0;
@@ -222,9 +259,12 @@ __global__ void __launch_bounds__(kRecThreads, 1) k_recover(RecArgs a) {
         }
       }
       CUPC_GRID_SYNC();
-      for (uint32_t w = gtid; w < V; w += gstride) {
-        const uint32_t K = ld_cg(&a.label[w]);
-        if (!ld_cg(&a.final_[K])) a.perm[atomicAdd(&a.rcnt[K], 1u)] = w;
+      for (uint32_t base = gwarp * 32; base < V; base += nwarps * 32) {
+        const uint32_t w = base + lane;
+        const uint32_t K = w < V ? ld_cg(&a.label[w]) : 0;
+        const bool live = w < V && !ld_cg(&a.final_[K]);
+        const uint32_t pos = warp_grab(a.rcnt, K, live);
+        if (live) a.perm[pos] = w;
       }
       CUPC_GRID_SYNC();
       nmem = ld_cg(&gc[GC_NMEMBERS]);
@@ -235,6 +275,8 @@ __global__ void __launch_bounds__(kRecThreads, 1) k_recover(RecArgs a) {
     // several spans is XORed into acc[K]; the last span to finish samples it.
     const uint32_t span = r == 0 ? 1u : kRecSpan;
     const uint32_t nspans = (nmem + span - 1) / span;
+    uint32_t st_k = kNoneU32, st_res = 0, nst = 0;  // this lane's stashed sample
+    uint64_t st_e = 0;
     for (uint32_t sp = gwarp; sp < nspans; sp += nwarps) {
       const uint32_t i0 = sp * span, cnt = min(span, nmem - i0);
       uint32_t mw = 0, mk = kNoneU32;
@@ -291,11 +333,21 @@ __global__ void __launch_bounds__(kRecThreads, 1) k_recover(RecArgs a) {
         if (mine) {
           uint64_t e = 0;
           const uint32_t res = warp_sample(acc, W, V, kchk, e);
-          if (lane == 0) take_sample(a, r, K, res, e);
+          if (lane == nst) {
+            st_k = K;
+            st_res = res;
+            st_e = e;
+          }
+          if (++nst == 32) {  // book 32 samples at once, one per lane
+            book_samples(a, r, st_k, st_res, st_e);
+            st_k = kNoneU32;
+            nst = 0;
+          }
         }
         i = j;
       }
     }
+    if (nst) book_samples(a, r, st_k, st_res, st_e);
     CUPC_GRID_SYNC();
     if (gtid == 0) gc[GC_ROUNDS] = r + 1;
     if (ld_cg(&gc[GC_NZ]) == 0) {
@@ -312,14 +364,15 @@ __global__ void __launch_bounds__(kRecThreads, 1) k_recover(RecArgs a) {
       uint64_t* bn = (iter & 1) ? a.best0 : a.best1;
       const uint32_t act = (iter & 1) ? GC_ACTIVE_ODD : GC_ACTIVE, act_next = (iter & 1) ? GC_ACTIVE : GC_ACTIVE_ODD;
       for (uint32_t K = gtid; K < V; K += gstride) {
-        const uint64_t e = ld_cg(&a.cand[K]);
-        if (e == kNone) continue;
-        const uint32_t ra = find_root(a.parent, ld_cg(&a.label[(uint32_t)(e / V)]), V);
-        const uint32_t rb = find_root(a.parent, ld_cg(&a.label[(uint32_t)(e % V)]), V);
+        const ulonglong2 c = __ldcg(&a.cand[K]);
+        if (c.x == kNone) continue;
+        const uint64_t e = c.x;
+        const uint32_t ra = find_root(a.parent, (uint32_t)(c.y >> 32), V);
+        const uint32_t rb = find_root(a.parent, (uint32_t)c.y, V);
         if (ra != rb) {
           atomicMin((unsigned long long*)&bc[ra], (unsigned long long)(e * V + rb));
           atomicMin((unsigned long long*)&bc[rb], (unsigned long long)(e * V + ra));
-          if (ld_cg(&gc[act]) == 0) atomicExch(&gc[act], 1u);
+          *(volatile uint32_t*)&gc[act] = 1u;
         }
       }
       CUPC_GRID_SYNC();
@@ -344,7 +397,7 @@ __global__ void __launch_bounds__(kRecThreads, 1) k_recover(RecArgs a) {
     // round's scratch
     for (uint32_t w = gtid; w < V; w += gstride) {
       a.rcnt[w] = 0;
-      a.cand[w] = kNone;
+      a.cand[w] = make_ulonglong2(kNone, 0);
       a.best0[w] = kNone;
       a.best1[w] = kNone;
       if (ld_cg(&a.label[w]) != w) continue;
@@ -361,14 +414,20 @@ __global__ void __launch_bounds__(kRecThreads, 1) k_recover(RecArgs a) {
     CUPC_GRID_SYNC();
     // new labels; the members of next round's live components are counted
     // here (a merged component is live; an unmerged one keeps its flag)
-    for (uint32_t w = gtid; w < V; w += gstride) {
-      const uint32_t K = ld_cg(&a.label[w]);
-      const uint32_t root = find_root(a.parent, K, V);
-      const uint32_t nl = ld_cg(&a.minv[root]);
-      const bool mg = ld_cg(&a.merged[root]) != 0;
-      a.label[w] = nl;
-      if (w == root && mg) a.final_[nl] = 0;
-      if (mg || !ld_cg(&a.final_[root])) atomicAdd(&a.rcnt[nl], 1u);
+    for (uint32_t base = gwarp * 32; base < V; base += nwarps * 32) {
+      const uint32_t w = base + lane;
+      uint32_t nl = 0;
+      bool live = false;
+      if (w < V) {
+        const uint32_t K = ld_cg(&a.label[w]);
+        const uint32_t root = find_root(a.parent, K, V);
+        nl = ld_cg(&a.minv[root]);
+        const bool mg = ld_cg(&a.merged[root]) != 0;
+        a.label[w] = nl;
+        if (w == root && mg) a.final_[nl] = 0;
+        live = mg || !ld_cg(&a.final_[root]);
+      }
+      warp_grab(a.rcnt, nl, live);
     }
     CUPC_GRID_SYNC();
   }
@@ -380,12 +439,11 @@ cudaError_t setup_recover(cupc_graph* g) {
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_recover, kRecThreads, 0);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
-  // enough CTAs to stream one layer at full bandwidth; fewer for small V so
-  // that the grid barriers stay cheap
-  uint32_t want = (g->V + 127) / 128;
-  if (want < 8) want = 8;
+  // about four vertices per warp in round 0 (every vertex samples its own
+  // sketch); fewer CTAs for small V keep the grid barriers cheap
+  uint32_t want = (g->V + 31) / 32;
+  if (want < 16) want = 16;
   uint32_t cap = (uint32_t)(per_sm * g->sms);
-  if (cap > (uint32_t)g->sms) cap = (uint32_t)g->sms;
   g->rec_grid = (int)(want < cap ? want : cap);
   return cudaSuccess;
 }
