@@ -51,7 +51,7 @@ Dims derive(uint32_t V, const cupc_params* p) {
 // Byte offsets of every device array inside the workspace.
 struct Layout {
   size_t sketch, keys, gc, cnt, cursor, rec, items, stage_edges, stage_ops, label, parent, minv, rcnt, roff,
-      perm, pcount, final_, merged, best, best2, cand, forest, forest_sorted, acc, log_ids, log_live,
+      perm, permb, pcount, final_, merged, best, best2, cand, forest, forest_sorted, acc, log_ids, log_live,
       log_ncand, total;
 };
 
@@ -80,6 +80,7 @@ Layout layout(const Dims& d) {
   l.rcnt = take(V * 4);
   l.roff = take(V * 4);
   l.perm = take(V * 4);
+  l.permb = take(V * 4);
   l.pcount = take(V * 4);
   l.final_ = take(V);
   l.merged = take(V);
@@ -191,6 +192,7 @@ cupc_status cupc_init(uint32_t V, uint64_t seed, const cupc_params* params, void
   g->rcnt = (uint32_t*)(b + l.rcnt);
   g->roff = (uint32_t*)(b + l.roff);
   g->perm = (uint32_t*)(b + l.perm);
+  g->permb = (uint32_t*)(b + l.permb);
   g->pcount = (uint32_t*)(b + l.pcount);
   g->final_ = (uint8_t*)(b + l.final_);
   g->merged = (uint8_t*)(b + l.merged);

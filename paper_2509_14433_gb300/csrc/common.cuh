@@ -29,7 +29,9 @@ constexpr uint32_t kSmemRows = 12;
 constexpr uint32_t kItemRecords = 512;
 // Threads of the recovery kernel and members per reduction work item.
 constexpr uint32_t kRecThreads = 256;
-constexpr uint32_t kRecSpan = 32;
+constexpr uint32_t kRecSpan = 32;  // also the largest "small" component
+// Members per CTA tile when reducing big components.
+constexpr uint32_t kRecTile = 256;
 constexpr uint32_t kWarpBuckets = 8;  // buckets per lane in the recovery: W <= 256
 // Bounded device-side waits give up after this long.
 constexpr uint64_t kWaitLimitNs = 2000000000ull;
@@ -52,6 +54,7 @@ enum : uint32_t {
   GC_BAR_COUNT = 13,
   GC_RECOVERIES = 15,
   GC_BATCHES = 16,   // update chunks applied
+  GC_NBIG = 17,      // members of big components this round
   GC_SLOTS = 32
 };
 
@@ -116,7 +119,8 @@ struct cupc_graph {
   uint32_t* minv;    // V
   uint32_t* rcnt;    // V
   uint32_t* roff;    // V
-  uint32_t* perm;    // V
+  uint32_t* perm;    // V: members of small components, grouped
+  uint32_t* permb;   // V: members of big components, grouped
   uint32_t* pcount;  // V: spans of a component reduced so far
   uint8_t* final_;   // V
   uint8_t* merged;   // V

@@ -29,7 +29,7 @@ struct RecArgs {
   const ulonglong2* sketch;
   const uint64_t* keys;
   uint32_t V, L, C, D, W;
-  uint32_t *label, *parent, *minv, *rcnt, *roff, *perm, *pcount;
+  uint32_t *label, *parent, *minv, *rcnt, *roff, *perm, *permb, *pcount;
   uint8_t *final_, *merged;
   uint64_t *best0, *best1, *forest, *log_ids;
   ulonglong2* cand;  // {edge, label[u] << 32 | label[v]} of a component's candidate
@@ -188,8 +188,14 @@ __device__ __forceinline__ void warp_xor_row(ulonglong2 (&acc)[kWarpBuckets], co
   }
 }
 
+constexpr uint32_t kBigFlag = 0x80000000u;  // roff[K] flag: K's members are in permb
+constexpr uint32_t kTileSegs = 10;           // components meeting one tile: <= 2 + kRecTile/33
+
 __global__ void __launch_bounds__(kRecThreads, 2) k_recover(RecArgs a) {
   __shared__ int s_ok;
+  __shared__ uint32_t t_w[kRecTile], t_k[kRecTile];
+  __shared__ ulonglong2 t_stage[kTileSegs][kRecThreads];
+  __shared__ uint32_t t_seg_k[kTileSegs], t_seg_b[kTileSegs], t_seg_e[kTileSegs];
   const uint32_t V = a.V, W = a.W, nb = gridDim.x, tid = threadIdx.x, lane = tid & 31;
   const uint32_t gtid = blockIdx.x * blockDim.x + tid, gstride = gridDim.x * blockDim.x;
   const uint32_t wpb = blockDim.x >> 5, gwarp = blockIdx.x * wpb + (tid >> 5), nwarps = gridDim.x * wpb;
@@ -220,6 +226,7 @@ __global__ void __launch_bounds__(kRecThreads, 2) k_recover(RecArgs a) {
     gc[GC_ACTIVE] = 0;
     gc[GC_ACTIVE_ODD] = 0;
     gc[GC_NMEMBERS] = 0;
+    gc[GC_NBIG] = 0;
     gc[GC_RECOVERIES] += 1;
   }
   for (uint32_t r = gtid; r < a.L; r += gstride) {
@@ -238,19 +245,26 @@ __global__ void __launch_bounds__(kRecThreads, 2) k_recover(RecArgs a) {
       for (uint32_t base = blockIdx.x * blockDim.x; base < V; base += gstride) {
         const uint32_t K = base + tid;
         const uint32_t c = K < V ? ld_cg(&a.rcnt[K]) : 0;
-        uint32_t inc = c;
+        const bool big = c > kRecSpan;
+        uint32_t is = big ? 0 : c, ib = big ? c : 0;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-          const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
-          if (lane >= (uint32_t)o) inc += y;
+          const uint32_t ys = __shfl_up_sync(0xffffffffu, is, o), yb = __shfl_up_sync(0xffffffffu, ib, o);
+          if (lane >= (uint32_t)o) {
+            is += ys;
+            ib += yb;
+          }
         }
-        const uint32_t tot = __shfl_sync(0xffffffffu, inc, 31);
-        uint32_t wbase = 0;
-        if (lane == 31 && tot) wbase = atomicAdd(&gc[GC_NMEMBERS], tot);
-        wbase = __shfl_sync(0xffffffffu, wbase, 31);
+        const uint32_t ts = __shfl_sync(0xffffffffu, is, 31), tb = __shfl_sync(0xffffffffu, ib, 31);
+        uint32_t bs = 0, bb = 0;
+        if (lane == 31 && ts) bs = atomicAdd(&gc[GC_NMEMBERS], ts);
+        if (lane == 31 && tb) bb = atomicAdd(&gc[GC_NBIG], tb);
+        bs = __shfl_sync(0xffffffffu, bs, 31);
+        bb = __shfl_sync(0xffffffffu, bb, 31);
         if (c) {
-          a.roff[K] = wbase + inc - c;
-          a.rcnt[K] = wbase + inc - c;  // scatter cursor, then the segment end
+          const uint32_t at = big ? bb + ib - c : bs + is - c;
+          a.roff[K] = big ? (at | kBigFlag) : at;
+          a.rcnt[K] = at;  // scatter cursor, then the segment end
         }
         if (K < V) {
           a.parent[K] = K;
@@ -264,7 +278,7 @@ __global__ void __launch_bounds__(kRecThreads, 2) k_recover(RecArgs a) {
         const uint32_t K = w < V ? ld_cg(&a.label[w]) : 0;
         const bool live = w < V && !ld_cg(&a.final_[K]);
         const uint32_t pos = warp_grab(a.rcnt, K, live);
-        if (live) a.perm[pos] = w;
+        if (live) ((ld_cg(&a.roff[K]) & kBigFlag) ? a.permb : a.perm)[pos] = w;
       }
       CUPC_GRID_SYNC();
       nmem = ld_cg(&gc[GC_NMEMBERS]);
@@ -273,6 +287,103 @@ __global__ void __launch_bounds__(kRecThreads, 2) k_recover(RecArgs a) {
     // ---- reduce + sample, one warp per span of members (round 0: one
     // vertex per span, every vertex is its own component). A component over
     // several spans is XORed into acc[K]; the last span to finish samples it.
+    if (r > 0) {
+      // big components (more than kRecSpan members): CTA tiles of up to
+      // kRecTile members, thread t XORs bucket t of every member (8 rows in
+      // flight);
+      // each component's part of the tile is staged in shared memory and
+      // sampled by one warp, or XORed into acc[K] when it spans several tiles
+      // (the last tile to finish samples it)
+      const uint32_t nbig = ld_cg(&gc[GC_NBIG]);
+      // about one tile per CTA: 16..kRecTile members, a multiple of 8
+      uint32_t tile = (nbig + nb - 1) / nb;
+      tile = min(kRecTile, max(16u, (tile + 7) & ~7u));
+      const uint32_t ntiles = (nbig + tile - 1) / tile;
+      for (uint32_t t = blockIdx.x; t < ntiles; t += nb) {
+        const uint32_t m0 = t * tile, cnt = min(tile, nbig - m0);
+        if (tid < cnt) {
+          const uint32_t w = ld_cg(&a.permb[m0 + tid]);
+          t_w[tid] = w;
+          t_k[tid] = ld_cg(&a.label[w]);
+        }
+        __syncthreads();
+        ulonglong2 acc1 = make_ulonglong2(0, 0);
+        uint32_t nseg = 0, segb = 0;
+        for (uint32_t m = 0; m < cnt; m += 8) {
+          ulonglong2 x[8];
+#pragma unroll
+          for (uint32_t k = 0; k < 8; k++) {
+            x[k] = make_ulonglong2(0, 0);
+            if (tid < W && m + k < cnt) x[k] = __ldg(a.sketch + ((size_t)r * V + t_w[m + k]) * W + tid);
+          }
+#pragma unroll
+          for (uint32_t k = 0; k < 8; k++) {
+            const uint32_t mm = m + k;
+            if (mm < cnt) {
+              acc1.x ^= x[k].x;
+              acc1.y ^= x[k].y;
+              if (mm + 1 == cnt || t_k[mm + 1] != t_k[mm]) {  // a component's part ends here
+                t_stage[nseg][tid] = acc1;
+                acc1 = make_ulonglong2(0, 0);
+                if (tid == 0) {
+                  t_seg_k[nseg] = t_k[mm];
+                  t_seg_b[nseg] = segb;
+                  t_seg_e[nseg] = mm + 1;
+                }
+                nseg++;
+                segb = mm + 1;
+              }
+            }
+          }
+        }
+        __syncthreads();
+        for (uint32_t sg = tid >> 5; sg < nseg; sg += wpb) {
+          const uint32_t K = t_seg_k[sg];
+          const uint32_t s0 = ld_cg(&a.roff[K]) & ~kBigFlag, s1 = ld_cg(&a.rcnt[K]);
+          const uint32_t ntk = (s1 - 1) / tile - s0 / tile + 1;
+          ulonglong2 acc[kWarpBuckets];
+#pragma unroll
+          for (uint32_t q = 0; q < kWarpBuckets; q++) acc[q] = t_stage[sg][lane + 32 * q];
+          bool mine = true;
+          if (ntk > 1) {
+            ulonglong2* dst = a.acc + (size_t)K * W;
+#pragma unroll
+            for (uint32_t q = 0; q < kWarpBuckets; q++) {
+              const uint32_t b = lane + 32 * q;
+              if (b < W && (acc[q].x | acc[q].y)) {
+                atomicXor(&dst[b].x, acc[q].x);
+                atomicXor(&dst[b].y, acc[q].y);
+              }
+            }
+            __threadfence();
+            uint32_t prev = 0;
+            if (lane == 0) prev = atomicAdd(&a.pcount[K], 1u);
+            mine = __shfl_sync(0xffffffffu, prev, 0) + 1 == ntk;
+            if (mine) {
+              __threadfence();
+#pragma unroll
+              for (uint32_t q = 0; q < kWarpBuckets; q++) {
+                const uint32_t b = lane + 32 * q;
+                acc[q] = make_ulonglong2(0, 0);
+                if (b < W) {
+                  acc[q] = __ldcg(dst + b);
+                  dst[b] = make_ulonglong2(0, 0);
+                }
+              }
+              if (lane == 0) a.pcount[K] = 0;
+            }
+          }
+          if (mine) {
+            uint64_t e = 0;
+            const uint32_t res = warp_sample(acc, W, V, kchk, e);
+            book_samples(a, r, lane == 0 ? K : kNoneU32, res, e);
+          }
+        }
+        __syncthreads();
+      }
+    }
+
+    // small components (and every vertex in round 0): one warp per span
     const uint32_t span = r == 0 ? 1u : kRecSpan;
     const uint32_t nspans = (nmem + span - 1) / span;
     uint32_t st_k = kNoneU32, st_res = 0, nst = 0;  // this lane's stashed sample
@@ -408,6 +519,7 @@ __global__ void __launch_bounds__(kRecThreads, 2) k_recover(RecArgs a) {
     if (gtid == 0) {
       gc[GC_NZ] = 0;
       gc[GC_NMEMBERS] = 0;
+      gc[GC_NBIG] = 0;
       gc[GC_ACTIVE] = 0;
       gc[GC_ACTIVE_ODD] = 0;
     }
@@ -463,6 +575,7 @@ cudaError_t launch_recover(cupc_graph* g, cudaStream_t s) {
   a.rcnt = g->rcnt;
   a.roff = g->roff;
   a.perm = g->perm;
+  a.permb = g->permb;
   a.pcount = g->pcount;
   a.final_ = g->final_;
   a.merged = g->merged;
