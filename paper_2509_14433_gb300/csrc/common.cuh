@@ -29,9 +29,9 @@ constexpr uint32_t kSmemRows = 12;
 constexpr uint32_t kItemRecords = 512;
 // Threads of the recovery kernel and members per reduction work item.
 constexpr uint32_t kRecThreads = 256;
-constexpr uint32_t kRecSpan = 32;  // also the largest "small" component
+constexpr uint32_t kRecSpan = 8;  // also the largest "small" component
 // Members per CTA tile when reducing big components.
-constexpr uint32_t kRecTile = 256;
+constexpr uint32_t kRecTile = 64;
 constexpr uint32_t kWarpBuckets = 8;  // buckets per lane in the recovery: W <= 256
 // Bounded device-side waits give up after this long.
 constexpr uint64_t kWaitLimitNs = 2000000000ull;

@@ -189,11 +189,12 @@ __device__ __forceinline__ void warp_xor_row(ulonglong2 (&acc)[kWarpBuckets], co
 }
 
 constexpr uint32_t kBigFlag = 0x80000000u;  // roff[K] flag: K's members are in permb
-constexpr uint32_t kTileSegs = 10;           // components meeting one tile: <= 2 + kRecTile/33
+constexpr uint32_t kTileSegs = 2 + kRecTile / (kRecSpan + 1);  // components meeting one tile
 
 __global__ void __launch_bounds__(kRecThreads, 2) k_recover(RecArgs a) {
   __shared__ int s_ok;
   __shared__ uint32_t t_w[kRecTile], t_k[kRecTile];
+  static_assert(kRecTile <= kRecThreads, "one member id per thread");
   __shared__ ulonglong2 t_stage[kTileSegs][kRecThreads];
   __shared__ uint32_t t_seg_k[kTileSegs], t_seg_b[kTileSegs], t_seg_e[kTileSegs];
   const uint32_t V = a.V, W = a.W, nb = gridDim.x, tid = threadIdx.x, lane = tid & 31;
