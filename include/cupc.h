@@ -148,6 +148,46 @@ cupc_status cupc_round_log(cupc_graph* g, uint32_t* live, uint32_t* ncand, uint6
 cupc_status cupc_profile_enable(cupc_graph* g, int on);
 cupc_status cupc_profile_read(cupc_graph* g, double* ms, uint64_t* launches, size_t n);
 
+/* ---- Batching (many batches, many graphs, few launches).
+ *
+ * cupc_update_batches: k consecutive batches of one graph stored back to
+ * back (edges/ops as in cupc_update_batch, batch i = entries
+ * [offsets[i], offsets[i+1]) of the arrays; offsets is a host array of k+1
+ * non-decreasing values). Sketch addition is XOR (App. A.1.1), so applying
+ * the concatenation equals applying the batches in order; they are applied
+ * as one batch, in chunks of max_batch edges. The group is validated as one:
+ * an invalid entry anywhere drops all k batches (sticky CUPC_EINVAL).
+ *
+ * cupc_batcher: applies one batch to each of k distinct graphs (k <= the
+ * max_graphs given at creation) with five launches in all, whatever k is.
+ * The launch sequence reads its arguments from a descriptor table in device
+ * memory; with use_cuda_graph it is captured once per launch shape as a
+ * CUDA graph and replayed, each call refreshing the table with one
+ * host-to-device copy from pinned memory. edges[i]/ops[i] are device
+ * pointers with n[i] <= that graph's max_batch entries. Results equal k
+ * separate cupc_update_batch calls, including the per-graph sticky error on
+ * an invalid batch. Calls on one batcher, and calls touching the same graph,
+ * must be ordered on one stream. The batcher owns a small device table, two
+ * pinned staging tables and the instantiated graphs. */
+cupc_status cupc_update_batches(cupc_graph* g, const uint32_t* edges, const int8_t* ops, const uint64_t* offsets,
+                                size_t k, cupc_stream stream);
+typedef struct cupc_batcher cupc_batcher;
+cupc_status cupc_batcher_create(uint32_t max_graphs, int use_cuda_graph, cupc_batcher** out);
+cupc_status cupc_batcher_update(cupc_batcher* b, cupc_graph* const* graphs, const uint32_t* const* edges,
+                                const int8_t* const* ops, const size_t* n, uint32_t k, cupc_stream stream);
+void cupc_batcher_destroy(cupc_batcher* b);
+
+/* Launch tunables of the update's apply kernel (results are identical for
+ * every setting; only speed changes): item_records = endpoint records per
+ * work item (64..512, 0 = 512), smem_rows = rows per column folded in shared
+ * memory (1..min(D, 16), 0 = min(D, 12)); deeper rows go straight to HBM),
+ * ctas_per_sm = resident CTAs per SM of the persistent grid (0 = as many as
+ * fit). CUPC_EINVAL (previous settings kept) when out of range.
+ * cupc_get_tuning: out4 = {item_records, smem_rows, ctas_per_sm, CTAs per SM
+ * in use}. */
+cupc_status cupc_set_tuning(cupc_graph* g, uint32_t item_records, uint32_t smem_rows, uint32_t ctas_per_sm);
+cupc_status cupc_get_tuning(const cupc_graph* g, uint32_t* out4);
+
 /* Derived parameters of a graph: out4 = {L, C, D, W}. */
 cupc_status cupc_get_params(const cupc_graph* g, uint32_t* out4);
 

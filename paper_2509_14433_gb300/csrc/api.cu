@@ -64,7 +64,7 @@ Layout layout(const Dims& d) {
     return at;
   };
   const size_t V = d.V, B = d.max_batch;
-  const size_t nitems = 2 * B / kItemRecords + (V < 2 * B ? V : 2 * B) + 1;
+  const size_t nitems = 2 * B / kMinItemRecords + (V < 2 * B ? V : 2 * B) + 1;
   l.sketch = take((size_t)d.L * V * d.W * sizeof(ulonglong2));
   l.keys = take((size_t)d.L * (d.C + 1) * sizeof(uint64_t));
   l.gc = take(GC_SLOTS * sizeof(uint32_t));
@@ -430,6 +430,36 @@ cupc_status cupc_profile_read(cupc_graph* g, double* ms, uint64_t* launches, siz
     ms[k] = k < (size_t)PC_N ? g->prof_ms[k] : 0.0;
     launches[k] = k < (size_t)PC_N ? g->prof_launches[k] : 0;
   }
+  return CUPC_OK;
+}
+
+cupc_status cupc_set_tuning(cupc_graph* g, uint32_t item_records, uint32_t smem_rows, uint32_t ctas_per_sm) {
+  if (!g) return CUPC_EINVAL;
+  if (item_records == 0) item_records = kItemRecords;
+  if (smem_rows == 0) smem_rows = g->D < kSmemRows ? g->D : kSmemRows;
+  if (item_records < kMinItemRecords || item_records > kItemRecords || smem_rows > kSmemRowsMax || smem_rows > g->D)
+    return CUPC_EINVAL;
+  const uint32_t old_items = g->item_records, old_rows = g->R, old_cps = g->apply_cps;
+  g->item_records = item_records;
+  g->R = smem_rows;
+  g->apply_cps = ctas_per_sm;
+  if (configure_apply(g) != cudaSuccess) {
+    cudaGetLastError();
+    g->item_records = old_items;
+    g->R = old_rows;
+    g->apply_cps = old_cps;
+    configure_apply(g);
+    return CUPC_EINVAL;
+  }
+  return CUPC_OK;
+}
+
+cupc_status cupc_get_tuning(const cupc_graph* g, uint32_t* out4) {
+  if (!g || !out4) return CUPC_EINVAL;
+  out4[0] = g->item_records;
+  out4[1] = g->R;
+  out4[2] = g->apply_cps;
+  out4[3] = (uint32_t)(g->apply_grid / (g->sms ? g->sms : 1));
   return CUPC_OK;
 }
 

@@ -24,9 +24,11 @@ constexpr uint32_t kNoneU32 = 0xFFFFFFFFu;
 
 // Rows per column that the update kernel folds in shared memory; deeper rows
 // (probability 2^-kSmemRows per index) are XORed straight into HBM.
-constexpr uint32_t kSmemRows = 12;
+constexpr uint32_t kSmemRows = 12;     // default
+constexpr uint32_t kSmemRowsMax = 16;
 // Records (endpoint incidences) per update work item.
-constexpr uint32_t kItemRecords = 512;
+constexpr uint32_t kItemRecords = 512;  // default and maximum
+constexpr uint32_t kMinItemRecords = 64;
 // Threads of the recovery kernel and members per reduction work item.
 constexpr uint32_t kRecThreads = 256;
 constexpr uint32_t kRecSpan = 8;  // also the largest "small" component
@@ -99,6 +101,7 @@ struct cupc_graph {
   bool dirty;
   int device, sms;
   int apply_threads, apply_smem, apply_grid;
+  uint32_t item_records, apply_cps;  // tunables: records per work item, CTAs per SM (0 = max)
   int rec_grid;
   // sketches and keys
   ulonglong2* sketch;  // L*V*W
@@ -108,7 +111,7 @@ struct cupc_graph {
   uint32_t* cnt;       // V
   uint32_t* cursor;    // V
   uint64_t* rec;       // 2*max_batch
-  uint4* items;        // 2*max_batch/kItemRecords + min(V, 2*max_batch) + 1
+  uint4* items;        // 2*max_batch/kMinItemRecords + min(V, 2*max_batch) + 1
   uint32_t* stage_edges;  // 2*max_batch
   int8_t* stage_ops;      // max_batch
   uint32_t* stage_pairs;  // 2*max_pairs
@@ -178,6 +181,7 @@ cudaError_t launch_keys(cupc_graph* g, cudaStream_t s);
 cudaError_t launch_update_chunk(cupc_graph* g, const uint32_t* edges, size_t n, cudaStream_t s);
 cudaError_t launch_validate(cupc_graph* g, const uint32_t* edges, const int8_t* ops, size_t n, cudaStream_t s);
 cudaError_t setup_update(cupc_graph* g);
+cudaError_t configure_apply(cupc_graph* g);
 cudaError_t raise_apply_smem_limit(int bytes);
 cudaError_t setup_recover(cupc_graph* g);
 cudaError_t launch_recover(cupc_graph* g, cudaStream_t s);

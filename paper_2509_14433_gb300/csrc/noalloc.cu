@@ -19,7 +19,7 @@ constexpr uint32_t kMaxEdges = CUPC_STATIC_MAX_EDGES;
 constexpr uint32_t kMaxKeys = 64 * 8;
 constexpr size_t kAlignS = 256;
 constexpr size_t align_s(size_t x) { return (x + kAlignS - 1) / kAlignS * kAlignS; }
-constexpr size_t kMaxItems = 2ull * kMaxEdges / kItemRecords + (kMaxV < 2ull * kMaxEdges ? kMaxV : 2ull * kMaxEdges) + 1;
+constexpr size_t kMaxItems = 2ull * kMaxEdges / kMinItemRecords + (kMaxV < 2ull * kMaxEdges ? kMaxV : 2ull * kMaxEdges) + 1;
 // byte offsets inside the static scratch
 constexpr size_t kOffGc = 0;
 constexpr size_t kOffKeys = align_s(kOffGc + GC_SLOTS * sizeof(uint32_t));
@@ -104,8 +104,9 @@ extern "C" cupc_status cupc_update_sketch_static(void* sketch, uint32_t V, uint6
   g.sms = ds->sms;
   g.P = ds->P;
   g.R = g.D < kSmemRows ? g.D : kSmemRows;
+  g.item_records = kItemRecords;
   g.apply_threads = (int)(((g.L * g.P) + 31) / 32 * 32);
-  g.apply_smem = (int)(kItemRecords * sizeof(ulonglong2) + (size_t)g.R * g.apply_threads * sizeof(ulonglong2));
+  g.apply_smem = (int)((size_t)(g.item_records + g.R * g.apply_threads) * sizeof(ulonglong2));
   // the set-up sized the launch for the widest graph; a narrower one fits
   g.apply_grid = ds->apply_grid;
   g.prof_on = false;

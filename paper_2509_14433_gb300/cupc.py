@@ -44,6 +44,12 @@ _SIGS = {
     "cupc_stats": (ctypes.c_int, [_P, _P, _P]),
     "cupc_round_log": (ctypes.c_int, [_P, _P, _P, _P, _sz, _P, _P]),
     "cupc_get_params": (ctypes.c_int, [_P, _P]),
+    "cupc_set_tuning": (ctypes.c_int, [_P, _u32, _u32, _u32]),
+    "cupc_update_batches": (ctypes.c_int, [_P, _P, _P, _P, _sz, _P]),
+    "cupc_batcher_create": (ctypes.c_int, [_u32, ctypes.c_int, _P]),
+    "cupc_batcher_update": (ctypes.c_int, [_P, _P, _P, _P, _P, _u32, _P]),
+    "cupc_batcher_destroy": (None, [_P]),
+    "cupc_get_tuning": (ctypes.c_int, [_P, _P]),
     "cupc_profile_enable": (ctypes.c_int, [_P, ctypes.c_int]),
     "cupc_profile_read": (ctypes.c_int, [_P, _P, _P, _sz]),
     "cupc_destroy": (None, [_P]),
@@ -145,6 +151,40 @@ def cupc_round_log(g, live, ncand, ids, cap: int, stream=None):
 
 def cupc_get_params(g, out4) -> int:
     return _lib.cupc_get_params(g, ptr(out4))
+
+
+def cupc_update_batches(g, edges, ops, offsets, k: int, stream=None) -> int:
+    """offsets: host uint64 array of k+1 entries."""
+    return _lib.cupc_update_batches(g, ptr(edges), ptr(ops), ptr(offsets), k, stream_handle(stream))
+
+
+def cupc_batcher_create(max_graphs: int, use_cuda_graph: bool = True):
+    """Returns (status, handle)."""
+    h = ctypes.c_void_p(0)
+    st = _lib.cupc_batcher_create(max_graphs, 1 if use_cuda_graph else 0, ctypes.byref(h))
+    return st, h.value
+
+
+def cupc_batcher_update(b, graphs, edges, ops, ns, stream=None) -> int:
+    """graphs: handles; edges/ops: device tensors or addresses; ns: sizes."""
+    k = len(graphs)
+    G = (ctypes.c_void_p * k)(*graphs)
+    E = (ctypes.c_void_p * k)(*[ptr(e) for e in edges])
+    O = (ctypes.c_void_p * k)(*[ptr(o) for o in ops])
+    N = (ctypes.c_size_t * k)(*ns)
+    return _lib.cupc_batcher_update(b, G, E, O, N, k, stream_handle(stream))
+
+
+def cupc_batcher_destroy(b) -> None:
+    _lib.cupc_batcher_destroy(b)
+
+
+def cupc_set_tuning(g, item_records: int, smem_rows: int, ctas_per_sm: int) -> int:
+    return _lib.cupc_set_tuning(g, item_records, smem_rows, ctas_per_sm)
+
+
+def cupc_get_tuning(g, out4) -> int:
+    return _lib.cupc_get_tuning(g, ptr(out4))
 
 
 def cupc_profile_enable(g, on: int) -> int:
