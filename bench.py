@@ -52,6 +52,7 @@ def workload_config(nE, nD):
     return {"workload": f"dense ER(V={V_DENSE}, p={P_DENSE}): {nE} inserts + {nD} deletes (10%) in batches of "
                         f"{BATCH}, then spanning forest",
             "V": V_DENSE, "batch": BATCH, "updates_per_step": nE + nD, "seed": SEED,
+            "apply_tuning": "autotuned table (paper_2509_14433_gb300/tuning_gb300.json) when present",
             "l2": "inputs larger than L2 (sketches 826 MB, edge stream ~600 MB): no flush"}
 
 
@@ -188,6 +189,8 @@ def run_gpu(args):
     forest_d = torch.empty(V_DENSE, dtype=torch.int64, device=dev)
     st, g = C.cupc_init(V_DENSE, SEED, None, None, stream)
     C.check(st, "cupc_init")
+    from paper_2509_14433_gb300 import autotune as AT
+    tuned = AT.apply(g, V_DENSE, BATCH)  # tuned apply setting for 2^20-edge batches, if the table has one
     prm = np.zeros(4, np.uint32)
     C.cupc_get_params(g, prm)
     L, Cc, Dd, W = (int(x) for x in prm)
@@ -278,6 +281,8 @@ def run_gpu(args):
 
     # ---- plain V=1024 toggle stream: updates/s and query latency
     plain = plain_stream_latency(torch, C, dev, stream)
+    batching = None if args.no_batching else batching_compare(torch, C, dev, stream)
+    serving = None if args.no_serving else serving_compare(torch, C, dev)
 
     # ---- roofline of the dominant kernel (sketch apply), measured live above
     counts_per_batch = []
@@ -325,10 +330,205 @@ def run_gpu(args):
                                      "dense_after_batch_p99": float(np.percentile(lat_dense, 99)),
                                      **plain},
                 "forest_edges": int(nf),
+                "batching": batching,
+                "serving": serving,
                 "cpu_baseline": cpu, "clocks": clk}
         print(json.dumps(line), flush=True)
     if pg is not None:
         pg.destroy_process_group()
+
+
+def batching_compare(torch, C, dev, stream, n_batches=48, rounds=30):
+    """Batched vs one-batch-per-launch (device-resident inputs, CUDA events).
+
+    uneven: R-MAT stream on V = 2^17 (a=.57, b=c=.19, d=.05, 20% deletes of
+    present edges, batch sizes log-uniform in [1k, 4M]), the first n_batches
+    batches: one cupc_update_batch per batch vs cupc_update_batches over the
+    back-to-back batches. many_graphs: 64 graphs with V log-uniform in
+    [2^10, 2^15], each receiving a 1k-edge batch per round: 64
+    cupc_update_batch calls per round vs one cupc_batcher_update call (CUDA
+    graph replay, and without the graph)."""
+    from paper_2509_14433_gb300 import autotune as AT
+    out = {}
+    # -- uneven batches of one graph
+    s = WL.RmatStream(levels=17, seed=3, device=dev)
+    bl = [s.next_batch() for _ in range(n_batches)]
+    sizes = [len(b[1]) for b in bl]
+    E = torch.cat([b[0].reshape(-1) for b in bl]).contiguous()
+    O = torch.cat([b[1] for b in bl]).contiguous()
+    offs = np.cumsum([0] + sizes).astype(np.uint64)
+    del bl, s
+    torch.cuda.empty_cache()
+    V = 1 << 17
+    st, g = C.cupc_init(V, 1, (0, 0, 0, 4 << 20), None, stream)
+    C.check(st)
+    AT.apply(g, V, int(np.median(sizes)))
+
+    def plain():
+        for i in range(n_batches):
+            C.check(C.cupc_update_batch(g, E.data_ptr() + 8 * int(offs[i]), O.data_ptr() + int(offs[i]),
+                                        sizes[i], stream))
+
+    def coalesced():
+        C.check(C.cupc_update_batches(g, E, O, offs, n_batches, stream))
+
+    res = {}
+    for name, fn in (("one_batch_per_launch", plain), ("coalesced", coalesced)):
+        C.cupc_reset(g, stream)
+        fn()
+        C.cupc_reset(g, stream)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        res[name] = int(offs[-1]) / (e0.elapsed_time(e1) / 1e3)
+    C.cupc_destroy(g)
+    del E, O
+    torch.cuda.empty_cache()
+    out["uneven_rmat_v131072"] = {"updates": int(offs[-1]), "batches": n_batches,
+                                  "batch_min": int(min(sizes)), "batch_max": int(max(sizes)),
+                                  "updates_per_s": res}
+    # -- many graphs, one small batch each per round
+    rng = WL.rng(17)
+    Vs = [int(2 ** x) for x in rng.uniform(10, 15, size=64)]
+    graphs = []
+    for i, V in enumerate(Vs):
+        st, h = C.cupc_init(V, 100 + i, (0, 0, 0, 1 << 16), None, stream)
+        C.check(st)
+        graphs.append(h)
+    m = 1000
+    bat = [(torch.from_numpy(WL.uniform_pairs(V, rounds * m, rng).reshape(-1)).to(dev),
+            torch.ones(rounds * m, dtype=torch.int8, device=dev)) for V in Vs]
+
+    def plain_many():
+        for r in range(rounds):
+            for h, (e, o) in zip(graphs, bat):
+                C.check(C.cupc_update_batch(h, e.data_ptr() + 8 * r * m, o.data_ptr() + r * m, m, stream))
+
+    res = {}
+    for name, use_graph in (("one_batch_per_launch", None), ("batcher_cuda_graph", True), ("batcher_no_graph", False)):
+        if use_graph is None:
+            fn = plain_many
+            b = None
+        else:
+            st, b = C.cupc_batcher_create(64, use_graph)
+            C.check(st)
+
+            def fn(b=b):
+                for r in range(rounds):
+                    C.check(C.cupc_batcher_update(b, graphs, [e.data_ptr() + 8 * r * m for e, _ in bat],
+                                                  [o.data_ptr() + r * m for _, o in bat], [m] * len(graphs), stream))
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        res[name] = rounds * m * len(graphs) / (e0.elapsed_time(e1) / 1e3)
+        if b is not None:
+            C.cupc_batcher_destroy(b)
+    for h in graphs:
+        C.cupc_destroy(h)
+    out["many_graphs_64x1k"] = {"graphs": len(graphs), "V_min": min(Vs), "V_max": max(Vs), "rounds": rounds,
+                                "updates_per_s": res}
+    return out
+
+
+def serving_compare(torch, C, dev, n_graphs=64, upd_range=(5e4, 5e5), seed=5):
+    """Serving workload (64 graphs, V log-uniform in [2^10, 2^15], ER(p)
+    insert/delete streams, p ~ U[0.1, 0.9], batches log-uniform in [1k, 1M],
+    a 1k-pair Connected batch after every 100k updates of a graph; each
+    graph's stream has log-uniform[upd_range] updates). All requests arrive
+    at once, round-robin over graphs. served: cupc_server (continuous
+    batching, multi-graph launches, overlapped query streams) with no memory
+    cap and with a cap of 25% of the graphs' total workspace (graphs wait for
+    admission and close when done); plain: one thread, one request at a time
+    through cupc_update_batch / cupc_query, each finished before the next.
+    Latency = arrival to completion; updates/s = all updates / makespan."""
+    streams = WL.serving_streams(n_graphs=n_graphs, upd_range=upd_range, seed=seed)
+    order = WL.round_robin(streams)
+    total_upd = sum(st[3] for st in streams)
+    maxb = 1 << 20
+    ws = [C.cupc_workspace_bytes(st[0], (0, 0, 0, maxb)) for st in streams]
+    out = {"graphs": n_graphs, "updates": int(total_upd), "requests": len(order),
+           "queries": sum(1 for _, s_ in order if s_[0] == "query")}
+
+    def served(cap_bytes):
+        st, srv = C.cupc_server_create(int(cap_bytes), n_graphs, maxb, 4)
+        C.check(st)
+        try:
+            ids = [C.cupc_server_open(srv, s_[0], s_[1])[1] for s_ in streams]
+            last = {}
+            for k, (i, _) in enumerate(order):
+                last[i] = k
+            keep, qt, ut = [], [], []
+            t0 = time.perf_counter()
+            for k, (i, stp) in enumerate(order):
+                if stp[0] == "update":
+                    e = np.ascontiguousarray(stp[1], np.uint32)
+                    o = np.ascontiguousarray(stp[2], np.int8)
+                    keep.append((e, o))
+                    r, t = C.cupc_server_update(srv, ids[i], e, o, len(o))
+                    ut.append(t)
+                else:
+                    p = np.ascontiguousarray(stp[1], np.uint32)
+                    ans = np.zeros(len(p), np.uint8)
+                    keep.append((p, ans))
+                    r, t = C.cupc_server_query(srv, ids[i], p, len(p), ans)
+                    qt.append(t)
+                C.check(r, "submit")
+                if k == last[i]:
+                    ut.append(C.cupc_server_close(srv, ids[i])[1])
+            lat = []
+            for t in ut:
+                C.check(C.cupc_server_wait(srv, t, 600000)[0], "update")
+            for t in qt:
+                r, l_us = C.cupc_server_wait(srv, t, 600000)
+                C.check(r, "query")
+                lat.append(l_us)
+            span = time.perf_counter() - t0
+            stats = np.zeros(8, np.uint64)
+            C.cupc_server_stats(srv, stats)
+            return {"updates_per_s": total_upd / span, "query_p50_us": float(np.percentile(lat, 50)),
+                    "query_p99_us": float(np.percentile(lat, 99)), "makespan_s": span,
+                    "update_launches": int(stats[2]), "update_requests": int(stats[3]),
+                    "admission_waits": int(stats[5])}
+        finally:
+            C.cupc_server_destroy(srv)
+
+    out["served_no_cap"] = served(sum(ws) * 1.02 + (256 << 20))
+    out["served_cap_25pct"] = served(0.25 * sum(ws))
+    # plain: one request at a time on the caller's thread
+    graphs = []
+    for s_ in streams:
+        r, g = C.cupc_init(s_[0], s_[1], (0, 0, 0, maxb), None, None)
+        C.check(r)
+        graphs.append(g)
+    try:
+        lat = []
+        t0 = time.perf_counter()
+        for i, stp in order:
+            if stp[0] == "update":
+                e = np.ascontiguousarray(stp[1], np.uint32)
+                o = np.ascontiguousarray(stp[2], np.int8)
+                C.check(C.cupc_update_batch(graphs[i], e, o, len(o), None))
+                torch.cuda.synchronize()
+            else:
+                p = np.ascontiguousarray(stp[1], np.uint32)
+                ans = np.zeros(len(p), np.uint8)
+                C.check(C.cupc_query(graphs[i], p, len(p), ans, None))
+                lat.append((time.perf_counter() - t0) * 1e6)
+        span = time.perf_counter() - t0
+        out["one_request_at_a_time"] = {"updates_per_s": total_upd / span,
+                                        "query_p50_us": float(np.percentile(lat, 50)),
+                                        "query_p99_us": float(np.percentile(lat, 99)), "makespan_s": span}
+    finally:
+        for g in graphs:
+            C.cupc_destroy(g)
+    return out
 
 
 def plain_stream_latency(torch, C, dev, stream):
@@ -403,6 +603,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="cupc", choices=["cupc", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batching", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
     args = ap.parse_args()
     if args.mode == "apply-profile":
         run_apply_profile(args)

@@ -177,10 +177,56 @@ cupc_status cupc_batcher_update(cupc_batcher* b, cupc_graph* const* graphs, cons
                                 const int8_t* const* ops, const size_t* n, uint32_t k, cupc_stream stream);
 void cupc_batcher_destroy(cupc_batcher* b);
 
+/* ---- Serving: many resident graphs, interleaved requests (Problem 2).
+ *
+ * A server owns a device arena of mem_bytes in which graphs are made
+ * resident (each takes cupc_workspace_bytes(V, {0,0,0,max_batch})), a pinned
+ * pool of pinned_bytes for request payloads, query_streams CUDA streams and
+ * one worker thread. cupc_server_open returns at once; the graph is admitted
+ * when its workspace fits (graphs wait in arrival order; closing a graph
+ * frees its space). Requests are copied at submission (host memory) and
+ * return a ticket. The worker serves continuously: in each cycle the next
+ * request of every resident graph with nothing in flight is started; a
+ * graph's consecutive update requests are joined into one batch (up to
+ * max_batch edges) and the batches of all such graphs go to the device in
+ * one multi-graph launch sequence (cupc_batcher, CUDA-graph replay); queries
+ * run on the query streams, overlapping with each other and with updates. A
+ * graph has at most one request in flight, so each graph's requests complete
+ * in submission order and give the same results as when it is served alone.
+ * cupc_server_wait blocks up to timeout_ms for a ticket (CUPC_ETIMEOUT if it
+ * is not done; the ticket stays valid) and returns its status (an invalid
+ * batch reports CUPC_EINVAL on its own ticket) and latency, submission to
+ * completion, in microseconds; a query's answers are in `out` by then.
+ * CUPC_ENOMEM from a submission: the pinned pool is full (retry after
+ * waiting) or the request can never fit. */
+typedef struct cupc_server cupc_server;
+typedef struct {
+  size_t mem_bytes;        /* device arena for resident graphs: the admission cap */
+  uint32_t max_graphs;     /* graphs open at once */
+  uint32_t max_batch;      /* edges per joined update batch, pairs per query (0: 1<<20) */
+  uint32_t query_streams;  /* queries in flight at once (0: 4) */
+  size_t pinned_bytes;     /* pinned payload pool (0: 256 MB) */
+} cupc_server_config;
+cupc_status cupc_server_create(const cupc_server_config* cfg, cupc_server** out);
+cupc_status cupc_server_open(cupc_server* s, uint32_t V, uint64_t seed, uint64_t* id);
+cupc_status cupc_server_update(cupc_server* s, uint64_t id, const uint32_t* edges, const int8_t* ops, size_t n,
+                               uint64_t* ticket);
+cupc_status cupc_server_query(cupc_server* s, uint64_t id, const uint32_t* pairs, size_t m, uint8_t* out,
+                              uint64_t* ticket);
+cupc_status cupc_server_close(cupc_server* s, uint64_t id, uint64_t* ticket);
+cupc_status cupc_server_wait(cupc_server* s, uint64_t ticket, uint32_t timeout_ms, double* latency_us);
+/* Sketches of a resident graph with no pending request (export layout). */
+cupc_status cupc_server_export(cupc_server* s, uint64_t id, void* dst, size_t bytes);
+/* out8: [0] edges applied, [1] query pairs answered, [2] update launch
+ * sequences, [3] update requests joined into them, [4] admissions, [5]
+ * cycles that waited for memory, [6] resident graphs, [7] graphs waiting. */
+cupc_status cupc_server_stats(cupc_server* s, uint64_t* out8);
+void cupc_server_destroy(cupc_server* s);
+
 /* Launch tunables of the update's apply kernel (results are identical for
  * every setting; only speed changes): item_records = endpoint records per
  * work item (64..512, 0 = 512), smem_rows = rows per column folded in shared
- * memory (1..min(D, 16), 0 = min(D, 12)); deeper rows go straight to HBM),
+ * memory (1..min(D, 16), 0 = min(D, 8)); deeper rows go straight to HBM),
  * ctas_per_sm = resident CTAs per SM of the persistent grid (0 = as many as
  * fit). CUPC_EINVAL (previous settings kept) when out of range.
  * cupc_get_tuning: out4 = {item_records, smem_rows, ctas_per_sm, CTAs per SM

@@ -1,0 +1,160 @@
+"""Autotuner for the update's apply kernel.
+
+The apply kernel has three launch tunables (cupc_set_tuning): endpoint
+records per work item, rows per column folded in shared memory, and CTAs per
+SM. None of them changes the result; they trade shared-memory footprint,
+occupancy and per-item overhead, and the best setting depends on how many
+records a vertex receives per batch, i.e. on V and the batch size.
+
+tune() times every candidate setting on the device (CUDA events recorded by
+the library around each apply launch) for each batch-size bucket (powers of
+four edges) and keeps the fastest; the table is stored as JSON keyed by GPU
+name and graph shape. apply() picks the bucket of a batch and sets it on a
+graph. Run `python -m paper_2509_14433_gb300.autotune --V 16384` on the
+target GPU to (re)write the table.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+DEFAULT_CACHE = os.path.join(HERE, "tuning_gb300.json")
+
+ITEM_RECORDS = (128, 256, 512)
+SMEM_ROWS = (8, 12, 16)
+CTAS_PER_SM = (0, 2)
+
+
+def bucket_of(n_edges: int) -> int:
+    """Bucket = floor(log4(n)), at least 5 (1024 edges)."""
+    b = 5
+    while (4 ** (b + 1)) <= n_edges:
+        b += 1
+    return b
+
+
+def shape_key(V: int, L: int, C: int, D: int) -> str:
+    return f"V={V},L={L},C={C},D={D}"
+
+
+def gpu_name() -> str:
+    import torch
+    return torch.cuda.get_device_name(0)
+
+
+def load(path: str = DEFAULT_CACHE) -> dict:
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def lookup(table: dict, V: int, L: int, C: int, D: int, n_edges: int):
+    """(item_records, smem_rows, ctas_per_sm) for this GPU, shape and batch
+    size, or None (defaults stay)."""
+    try:
+        import torch
+        name = torch.cuda.get_device_name(0)
+    except Exception:
+        return None
+    ent = table.get(name, {}).get(shape_key(V, L, C, D))
+    if not ent:
+        return None
+    b = bucket_of(n_edges)
+    keys = sorted(int(k) for k in ent)
+    best = min(keys, key=lambda k: abs(k - b))
+    return tuple(ent[str(best)]["setting"])
+
+
+def apply(g, V: int, n_edges: int, table: dict | None = None) -> bool:
+    """Set the tuned setting for a batch of n_edges on graph handle g."""
+    from . import cupc as C
+    p = np.zeros(4, np.uint32)
+    C.cupc_get_params(g, p)
+    L, Cc, D, _ = (int(x) for x in p)
+    s = lookup(load() if table is None else table, V, L, Cc, D, n_edges)
+    if s is None:
+        return False
+    return C.cupc_set_tuning(g, *s) == C.CUPC_OK
+
+
+def _time_setting(C, g, e_d, o_d, n, reps, setting):
+    if C.cupc_set_tuning(g, *setting) != C.CUPC_OK:
+        return None
+    C.check(C.cupc_update_batch(g, e_d, o_d, n, None))  # warm
+    C.cupc_profile_enable(g, 1)
+    for _ in range(reps):
+        C.check(C.cupc_update_batch(g, e_d, o_d, n, None))
+    ms = np.zeros(8)
+    nl = np.zeros(8, np.uint64)
+    C.cupc_profile_read(g, ms, nl, 8)
+    C.cupc_profile_enable(g, 0)
+    return float(ms[2]) / max(1, int(nl[2]))
+
+
+def tune(V: int, sizes=None, reps: int = 3, seed: int = 1, path: str = DEFAULT_CACHE, verbose: bool = True):
+    """Time every setting per batch-size bucket on a graph of V vertices
+    with uniform random batches; merge the winners into the JSON table."""
+    import torch
+
+    from . import cupc as C
+    from . import workloads as WL
+    if sizes is None:
+        sizes = [4 ** b for b in range(5, 12) if 4 ** b <= (1 << 22)]
+    st, g = C.cupc_init(V, seed, (0, 0, 0, max(sizes)), None, None)  # each batch is one launch
+    C.check(st, "cupc_init")
+    p = np.zeros(4, np.uint32)
+    C.cupc_get_params(g, p)
+    L, Cc, D, _ = (int(x) for x in p)
+    rng = WL.rng(seed)
+    table = load(path)
+    ent = table.setdefault(gpu_name(), {}).setdefault(shape_key(V, L, Cc, D), {})
+    try:
+        for n in sizes:
+            E = WL.uniform_pairs(V, n, rng)
+            e_d = torch.from_numpy(E.reshape(-1)).cuda()
+            o_d = torch.ones(n, dtype=torch.int8, device="cuda")
+            results = []
+            for it in ITEM_RECORDS:
+                for rows in SMEM_ROWS:
+                    if rows > D:
+                        continue
+                    for cps in CTAS_PER_SM:
+                        t = _time_setting(C, g, e_d, o_d, n, reps, (it, rows, cps))
+                        if t is not None:
+                            results.append((t, (it, rows, cps)))
+            results.sort()
+            best_t, best = results[0]
+            default = [t for t, s in results if s == (512, min(8, D), 0)]
+            ent[str(bucket_of(n))] = {"setting": list(best), "apply_ms": best_t,
+                                      "default_ms": default[0] if default else None, "edges": n}
+            if verbose:
+                print(f"V={V} n={n}: best {best} {best_t:.4f} ms (default {default[0] if default else '-'} ms)",
+                      flush=True)
+    finally:
+        C.cupc_destroy(g)
+    with open(path + ".tmp", "w") as f:
+        json.dump(table, f, indent=1, sort_keys=True)
+    os.replace(path + ".tmp", path)
+    return ent
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--V", type=int, nargs="+", default=[16384])
+    ap.add_argument("--max-edges", type=int, default=1 << 22)
+    ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--out", default=DEFAULT_CACHE)
+    a = ap.parse_args()
+    for V in a.V:
+        sizes = [4 ** b for b in range(5, 12) if 4 ** b <= a.max_edges]
+        tune(V, sizes, reps=a.reps, path=a.out)
+
+
+if __name__ == "__main__":
+    main()

@@ -24,7 +24,7 @@ constexpr uint32_t kNoneU32 = 0xFFFFFFFFu;
 
 // Rows per column that the update kernel folds in shared memory; deeper rows
 // (probability 2^-kSmemRows per index) are XORed straight into HBM.
-constexpr uint32_t kSmemRows = 12;     // default
+constexpr uint32_t kSmemRows = 8;      // default (the autotuner's usual pick on GB300)
 constexpr uint32_t kSmemRowsMax = 16;
 // Records (endpoint incidences) per update work item.
 constexpr uint32_t kItemRecords = 512;  // default and maximum

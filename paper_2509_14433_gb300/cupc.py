@@ -49,6 +49,15 @@ _SIGS = {
     "cupc_batcher_create": (ctypes.c_int, [_u32, ctypes.c_int, _P]),
     "cupc_batcher_update": (ctypes.c_int, [_P, _P, _P, _P, _P, _u32, _P]),
     "cupc_batcher_destroy": (None, [_P]),
+    "cupc_server_create": (ctypes.c_int, [_P, _P]),
+    "cupc_server_open": (ctypes.c_int, [_P, _u32, _u64, _P]),
+    "cupc_server_update": (ctypes.c_int, [_P, _u64, _P, _P, _sz, _P]),
+    "cupc_server_query": (ctypes.c_int, [_P, _u64, _P, _sz, _P, _P]),
+    "cupc_server_close": (ctypes.c_int, [_P, _u64, _P]),
+    "cupc_server_wait": (ctypes.c_int, [_P, _u64, _u32, _P]),
+    "cupc_server_export": (ctypes.c_int, [_P, _u64, _P, _sz]),
+    "cupc_server_stats": (ctypes.c_int, [_P, _P]),
+    "cupc_server_destroy": (None, [_P]),
     "cupc_get_tuning": (ctypes.c_int, [_P, _P]),
     "cupc_profile_enable": (ctypes.c_int, [_P, ctypes.c_int]),
     "cupc_profile_read": (ctypes.c_int, [_P, _P, _P, _sz]),
@@ -177,6 +186,63 @@ def cupc_batcher_update(b, graphs, edges, ops, ns, stream=None) -> int:
 
 def cupc_batcher_destroy(b) -> None:
     _lib.cupc_batcher_destroy(b)
+
+
+class cupc_server_config(ctypes.Structure):
+    _fields_ = [("mem_bytes", _sz), ("max_graphs", _u32), ("max_batch", _u32), ("query_streams", _u32),
+                ("pinned_bytes", _sz)]
+
+
+def cupc_server_create(mem_bytes: int, max_graphs: int, max_batch: int = 0, query_streams: int = 0,
+                       pinned_bytes: int = 0):
+    """Returns (status, handle)."""
+    cfg = cupc_server_config(mem_bytes, max_graphs, max_batch, query_streams, pinned_bytes)
+    h = ctypes.c_void_p(0)
+    st = _lib.cupc_server_create(ctypes.byref(cfg), ctypes.byref(h))
+    return st, h.value
+
+
+def cupc_server_open(s, V: int, seed: int):
+    i = ctypes.c_uint64(0)
+    st = _lib.cupc_server_open(s, V, seed & (2**64 - 1), ctypes.byref(i))
+    return st, i.value
+
+
+def cupc_server_update(s, gid: int, edges, ops, n: int):
+    t = ctypes.c_uint64(0)
+    st = _lib.cupc_server_update(s, gid, ptr(edges), ptr(ops), n, ctypes.byref(t))
+    return st, t.value
+
+
+def cupc_server_query(s, gid: int, pairs, m: int, out):
+    t = ctypes.c_uint64(0)
+    st = _lib.cupc_server_query(s, gid, ptr(pairs), m, ptr(out), ctypes.byref(t))
+    return st, t.value
+
+
+def cupc_server_close(s, gid: int):
+    t = ctypes.c_uint64(0)
+    st = _lib.cupc_server_close(s, gid, ctypes.byref(t))
+    return st, t.value
+
+
+def cupc_server_wait(s, ticket: int, timeout_ms: int = 60000):
+    """Returns (status, latency_us)."""
+    lat = ctypes.c_double(0.0)
+    st = _lib.cupc_server_wait(s, ticket, timeout_ms, ctypes.byref(lat))
+    return st, lat.value
+
+
+def cupc_server_export(s, gid: int, dst, nbytes: int) -> int:
+    return _lib.cupc_server_export(s, gid, ptr(dst), nbytes)
+
+
+def cupc_server_stats(s, out8) -> int:
+    return _lib.cupc_server_stats(s, ptr(out8))
+
+
+def cupc_server_destroy(s) -> None:
+    _lib.cupc_server_destroy(s)
 
 
 def cupc_set_tuning(g, item_records: int, smem_rows: int, ctas_per_sm: int) -> int:

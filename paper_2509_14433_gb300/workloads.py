@@ -245,3 +245,88 @@ class RmatStream:
         ops = t.cat([t.full((dels.numel(),), -1, dtype=t.int8, device=self.device),
                      t.ones(ins.numel(), dtype=t.int8, device=self.device)])
         return edges, ops
+
+
+# ---- many independent graphs with interleaved requests (serving) ----------
+
+def _distinct_pairs(V: int, k: int, g: np.random.Generator, exclude: np.ndarray | None = None) -> np.ndarray:
+    """k distinct uniform pair ids u*V+v (u<v), none in sorted `exclude`."""
+    out = np.zeros(0, np.int64)
+    while out.size < k:
+        need = k - out.size
+        u = g.integers(0, V, size=2 * need + 16)
+        v = g.integers(0, V, size=2 * need + 16)
+        ok = u != v
+        ids = np.minimum(u, v)[ok] * V + np.maximum(u, v)[ok]
+        if exclude is not None and exclude.size:
+            ids = ids[~np.isin(ids, exclude)]
+        out = np.unique(np.concatenate([out, ids]))
+        if out.size > k:
+            out = g.permutation(out)[:k]
+    return g.permutation(out)
+
+
+def serving_streams(n_graphs: int = 64, v_exp=(10.0, 15.0), p_range=(0.1, 0.9), upd_range=(1e5, 1e6),
+                    batch_range=(1000, 1 << 20), rho: int = 100_000, q_size: int = 1000, seed: int = 1):
+    """Per-graph request lists for the serving workload.
+
+    Graph i has V = floor(2^U[v_exp]) vertices and an ER(p), p ~ U[p_range],
+    insert/delete stream of U ~ log-uniform[upd_range] updates: first the
+    edges of ER(p) in a random order (a prefix of that order is a uniform
+    random set of distinct pairs; at most 70% of the updates), then uniform
+    toggles (distinct within a batch: insert if absent, delete if present).
+    Updates come in batches of log-uniform size in batch_range; after every
+    `rho` updates of the graph a batch of q_size uniform Connected pairs
+    follows. Returns [(V, seed_i, steps)] with steps as in toggle_stream and
+    the number of updates of each graph."""
+    g = rng(seed)
+    out = []
+    for i in range(n_graphs):
+        V = int(2 ** g.uniform(*v_exp))
+        p = g.uniform(*p_range)
+        total = int(np.exp(g.uniform(np.log(upd_range[0]), np.log(upd_range[1]))))
+        n_ins = int(min(round(p * V * (V - 1) / 2), 0.7 * total))
+        present = _distinct_pairs(V, n_ins, g)
+        steps, done, next_q = [], 0, rho
+        pos = 0
+        while done < total:
+            b = int(np.exp(g.uniform(np.log(batch_range[0]), np.log(batch_range[1]))))
+            b = min(b, total - done)
+            if pos < n_ins:
+                ids = present[pos:pos + b]
+                pos += ids.size
+                ops = np.ones(ids.size, np.int8)
+            else:
+                ids = _distinct_pairs(V, b, g)
+                ops = np.ones(ids.size, np.int8)
+                cur = np.sort(present[:pos]) if pos else np.zeros(0, np.int64)
+                hit = np.isin(ids, cur)
+                ops[hit] = -1
+                keep = np.concatenate([cur[~np.isin(cur, ids[hit])], ids[~hit]])
+                present = keep
+                pos = keep.size
+                n_ins = pos
+            e = np.stack([ids // V, ids % V], 1).astype(np.uint32)
+            steps.append(("update", e, ops))
+            done += ids.size
+            while done >= next_q:
+                steps.append(("query", uniform_pairs(V, q_size, g, distinct=False)))
+                next_q += rho
+        out.append((V, 1000 + i, steps, done))
+    return out
+
+
+def round_robin(streams):
+    """Arrival order: one step of each graph in turn, as (graph index, step)."""
+    idx = [0] * len(streams)
+    order = []
+    live = True
+    while live:
+        live = False
+        for i, st in enumerate(streams):
+            steps = st[2]
+            if idx[i] < len(steps):
+                order.append((i, steps[idx[i]]))
+                idx[i] += 1
+                live = True
+    return order

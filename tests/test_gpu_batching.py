@@ -109,3 +109,40 @@ def test_batcher_rejects_bad_calls():
         assert C.cupc_batcher_update(b, [b2.h], [h], [np.ones(2, np.int8)], [2]) == C.CUPC_EINVAL  # host memory
     finally:
         C.cupc_batcher_destroy(b)
+
+
+def test_every_tuning_gives_identical_sketches():
+    # the apply kernel's tunables change speed only, never the result
+    from paper_2509_14433_gb300 import autotune as AT
+    from paper_2509_14433_gb300 import cupc as C
+    V = 3000
+    E = WL.er_edges(V, 0.01, 5)
+    ref = O.Graph(V, 8)
+    ref.update(E)
+    want = ref.export()
+    for setting in [(64, 8, 0), (128, 16, 2), (512, 12, 0), (256, 1, 4), (512, 16, 1)]:
+        dev = _dev(V, 8)
+        assert C.cupc_set_tuning(dev.h, *setting) == 0
+        out = np.zeros(4, np.uint32)
+        C.cupc_get_tuning(dev.h, out)
+        assert tuple(int(x) for x in out[:3]) == setting
+        assert dev.update(E) == 0
+        assert np.array_equal(dev.export(), want), setting
+    dev = _dev(V, 8)
+    assert C.cupc_set_tuning(dev.h, 32, 12, 0) == C.CUPC_EINVAL  # records per item below 64
+    assert C.cupc_set_tuning(dev.h, 512, 17, 0) == C.CUPC_EINVAL  # more than 16 shared rows
+    assert AT.bucket_of(1000) == 5 and AT.bucket_of(4096) == 6 and AT.bucket_of(1 << 20) == 10
+
+
+def test_autotuner_writes_a_table_and_applies_it(tmp_path):
+    from paper_2509_14433_gb300 import autotune as AT
+    from paper_2509_14433_gb300 import cupc as C
+    path = str(tmp_path / "t.json")
+    ent = AT.tune(2048, sizes=[4096, 65536], reps=1, path=path, verbose=False)
+    assert set(ent) == {"6", "8"}
+    table = AT.load(path)
+    dev = _dev(2048, 1)
+    assert AT.apply(dev.h, 2048, 65536, table)
+    out = np.zeros(4, np.uint32)
+    C.cupc_get_tuning(dev.h, out)
+    assert list(int(x) for x in out[:3]) == ent["8"]["setting"]
