@@ -240,6 +240,15 @@ cupc_status cupc_get_params(const cupc_graph* g, uint32_t* out4);
 void cupc_destroy(cupc_graph* g);
 const char* cupc_status_string(cupc_status s);
 
+/* Self-test of failure detection on the device: every wait a library kernel
+ * makes on other CTAs is bounded. This launches `ctas` (2..64) co-resident
+ * CTAs that meet at a grid barrier, of which CTA `absent_cta` (-1: none)
+ * never arrives; the waiting CTAs give up after limit_us microseconds
+ * (1..1e6), record the timeout and return. Synchronises `stream`. Returns
+ * CUPC_ETIMEOUT when the wait ran out, CUPC_OK when every CTA arrived; the
+ * CUDA context stays usable either way. */
+cupc_status cupc_selftest_wait_timeout(uint32_t ctas, uint32_t limit_us, int absent_cta, cupc_stream stream);
+
 /* ---- Update without any device allocation (the paper has no counterpart).
  *
  * For callers that cannot call cudaMalloc at all: code whose device memory

@@ -50,7 +50,7 @@ Dims derive(uint32_t V, const cupc_params* p) {
 
 // Byte offsets of every device array inside the workspace.
 struct Layout {
-  size_t sketch, keys, gc, cnt, cursor, rec, items, stage_edges, stage_ops, label, parent, minv, rcnt, roff,
+  size_t sketch, keys, gc, cnt, cursor, rec, recw, items, stage_edges, stage_ops, label, parent, minv, rcnt, roff,
       perm, permb, pcount, final_, merged, best, best2, cand, forest, forest_sorted, acc, log_ids, log_live,
       log_ncand, total;
 };
@@ -64,13 +64,14 @@ Layout layout(const Dims& d) {
     return at;
   };
   const size_t V = d.V, B = d.max_batch;
-  const size_t nitems = 2 * B / kMinItemRecords + (V < 2 * B ? V : 2 * B) + 1;
+  const size_t nitems = 4 * B / kMinItemRecords + (V < 2 * B ? V : 2 * B) + 1;
   l.sketch = take((size_t)d.L * V * d.W * sizeof(ulonglong2));
   l.keys = take((size_t)d.L * (d.C + 1) * sizeof(uint64_t));
   l.gc = take(GC_SLOTS * sizeof(uint32_t));
   l.cnt = take(V * 4);
   l.cursor = take(V * 4);
   l.rec = take(2 * B * 8);
+  l.recw = take(2 * B * 4);
   l.items = take(nitems * sizeof(uint4));
   l.stage_edges = take(2 * B * 4);
   l.stage_ops = take(B);
@@ -181,6 +182,7 @@ cupc_status cupc_init(uint32_t V, uint64_t seed, const cupc_params* params, void
   g->cnt = (uint32_t*)(b + l.cnt);
   g->cursor = (uint32_t*)(b + l.cursor);
   g->rec = (uint64_t*)(b + l.rec);
+  g->recw = (uint32_t*)(b + l.recw);
   g->items = (uint4*)(b + l.items);
   g->stage_edges = (uint32_t*)(b + l.stage_edges);
   g->stage_ops = (int8_t*)(b + l.stage_ops);

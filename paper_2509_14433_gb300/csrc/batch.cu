@@ -29,13 +29,15 @@ struct alignas(16) InstDesc {
   uint32_t* cnt;
   uint32_t* cursor;
   uint64_t* rec;
+  uint32_t* recw;
   uint4* items;
   uint32_t* gc;
   uint64_t edge_base;  // first edge of this graph in the launch's edge space
   uint32_t n, V, L, C, D, W, P, R, item_records;
   uint32_t item_base;  // first work item of this graph (set by k_plan_m)
   uint32_t nitems;     // set by k_plan_m
-  uint32_t pad;
+  uint32_t nd;         // direct-path records (set by k_plan_m)
+  uint32_t pad[3];
 };
 
 struct alignas(16) BatchHead {
@@ -105,52 +107,20 @@ __global__ void k_count_m(const BatchHead* __restrict__ h) {
   }
 }
 
-// One CTA per graph: cursors and work items as k_plan; the last CTA to
-// finish lays the graphs' work items end to end.
+// One CTA per graph: cursors and work items (plan_vertices); the last CTA
+// to finish lays the graphs' work items end to end.
 __global__ void __launch_bounds__(1024) k_plan_m(BatchHead* __restrict__ h) {
-  __shared__ uint32_t sa[32], sb[32];
   __shared__ bool s_last;
   InstDesc* d = const_cast<InstDesc*>(descs_of(h));
   const uint32_t k = h->k, b = blockIdx.x;
   if (b >= k) return;
   InstDesc& g = d[b];
-  uint32_t carry_rec = 0, carry_item = 0;
+  uint32_t nitems = 0, nd = 0;
   const bool dropped = (ld_cg(&g.gc[GC_ERR]) & kErrInval) != 0;
-  if (!dropped && g.n > 0) {
-    for (uint32_t base = 0; base < g.V; base += 4 * blockDim.x) {
-      const uint32_t w0 = base + 4 * threadIdx.x;
-      uint32_t c[4], ni[4], lr = 0, li = 0;
-#pragma unroll
-      for (int q = 0; q < 4; q++) {
-        c[q] = (w0 + q < g.V) ? g.cnt[w0 + q] : 0;
-        ni[q] = (c[q] + g.item_records - 1) / g.item_records;
-        lr += c[q];
-        li += ni[q];
-      }
-      uint32_t er, ei, tr, ti;
-      block_scan2(lr, li, er, ei, tr, ti, sa, sb);
-      uint32_t pr = carry_rec + er, pi = carry_item + ei;
-#pragma unroll
-      for (int q = 0; q < 4; q++) {
-        const uint32_t w = w0 + q;
-        if (w < g.V) {
-          g.cursor[w] = pr;
-          g.cnt[w] = 0;
-          for (uint32_t z = 0; z < ni[q]; z++) {
-            const uint32_t bb = pr + z * g.item_records;
-            const uint32_t ee = min(pr + c[q], bb + g.item_records);
-            g.items[pi + z] = make_uint4(w, bb, ee, ni[q] == 1 ? 1u : 0u);
-          }
-        }
-        pr += c[q];
-        pi += ni[q];
-      }
-      carry_rec += tr;
-      carry_item += ti;
-    }
-  }
+  if (!dropped && g.n > 0) nitems = plan_vertices(g.cnt, g.cursor, g.items, g.V, g.item_records, &nd);
   if (threadIdx.x == 0) {
-    g.nitems = carry_item;
+    g.nitems = nitems;
+    g.nd = nd;
     if (!dropped && g.n > 0) g.gc[GC_BATCHES] += 1;
     __threadfence();
     s_last = atomicAdd(&h->plans_done, 1u) == k - 1;
@@ -178,8 +148,12 @@ __global__ void k_scatter_m(const BatchHead* __restrict__ h) {
     const uint64_t j = i - g.edge_base;
     const uint32_t u = g.edges[2 * j], v = g.edges[2 * j + 1];
     const uint64_t idx = (uint64_t)min(u, v) * g.V + max(u, v);
-    g.rec[atomicAdd(&g.cursor[u], 1u)] = idx;
-    g.rec[atomicAdd(&g.cursor[v], 1u)] = idx;
+    const uint32_t pu = atomicAdd(&g.cursor[u], 1u), pv = atomicAdd(&g.cursor[v], 1u);
+    g.rec[pu] = idx;
+    g.rec[pv] = idx;
+    const uint32_t nd = ld_cg(&g.nd);
+    if (pu < nd) g.recw[pu] = u;
+    if (pv < nd) g.recw[pv] = v;
   }
 }
 
@@ -190,6 +164,7 @@ __global__ void k_apply_m(BatchHead* __restrict__ h, uint32_t rmax, uint32_t ite
   extern __shared__ __align__(16) unsigned char smem_raw[];
   ulonglong2* s_xp = reinterpret_cast<ulonglong2*>(smem_raw);
   ulonglong2* s_acc = s_xp + items_max;
+  uint32_t* s_w = reinterpret_cast<uint32_t*>(s_acc + (size_t)rmax * blockDim.x);
   __shared__ uint32_t s_item;
   const InstDesc* d = descs_of(h);
   const uint32_t k = h->k;
@@ -211,6 +186,13 @@ __global__ void k_apply_m(BatchHead* __restrict__ h, uint32_t rmax, uint32_t ite
       l = apply_lane(g.keys, g.L, g.C, g.D, g.P, g.R);
     }
     const uint4 item = g.items[it - ld_cg(&g.item_base)];
+    if (item.x == kDirectItem) {
+      if (g.D > 32)
+        apply_direct<true>(l, g.sketch, g.V, g.W, g.rec + item.y, g.recw + item.y, item.z - item.y, g.D, s_xp, s_w);
+      else
+        apply_direct<false>(l, g.sketch, g.V, g.W, g.rec + item.y, g.recw + item.y, item.z - item.y, g.D, s_xp, s_w);
+      continue;
+    }
     ulonglong2* gb = g.sketch + ((size_t)l.layer * g.V + item.x) * g.W + l.jbase;
     if (g.D > 32)
       apply_item<true>(l, gb, g.rec + item.y, item.z - item.y, item.w != 0, g.D, g.R, s_xp, my_rows, rs);
@@ -274,7 +256,7 @@ cudaError_t get_exec(cupc_batcher* b, uint32_t threads, uint32_t rmax, uint32_t 
   x.threads = threads;
   x.rmax = rmax;
   x.imax = imax;
-  x.apply_smem = (int)((size_t)(imax + rmax * threads) * sizeof(ulonglong2));
+  x.apply_smem = (int)((size_t)(imax + rmax * threads) * sizeof(ulonglong2) + (size_t)imax * sizeof(uint32_t));
   cudaFuncAttributes fa;
   cudaError_t e = cudaFuncGetAttributes(&fa, k_apply_m);
   if (e != cudaSuccess) return e;
@@ -364,6 +346,7 @@ cupc_status cupc_batcher_update(cupc_batcher* b, cupc_graph* const* graphs, cons
     x.cnt = g->cnt;
     x.cursor = g->cursor;
     x.rec = g->rec;
+    x.recw = g->recw;
     x.items = g->items;
     x.gc = g->gc;
     x.edge_base = base;

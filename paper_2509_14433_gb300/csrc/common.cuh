@@ -57,6 +57,7 @@ enum : uint32_t {
   GC_RECOVERIES = 15,
   GC_BATCHES = 16,   // update chunks applied
   GC_NBIG = 17,      // members of big components this round
+  GC_NDIRECT = 18,   // direct-path records of the current chunk
   GC_SLOTS = 32
 };
 
@@ -111,7 +112,8 @@ struct cupc_graph {
   uint32_t* cnt;       // V
   uint32_t* cursor;    // V
   uint64_t* rec;       // 2*max_batch
-  uint4* items;        // 2*max_batch/kMinItemRecords + min(V, 2*max_batch) + 1
+  uint32_t* recw;      // 2*max_batch: vertex of each direct-path record
+  uint4* items;        // 4*max_batch/kMinItemRecords + min(V, 2*max_batch) + 1
   uint32_t* stage_edges;  // 2*max_batch
   int8_t* stage_ops;      // max_batch
   uint32_t* stage_pairs;  // 2*max_pairs

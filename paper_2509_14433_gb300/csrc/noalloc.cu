@@ -19,14 +19,15 @@ constexpr uint32_t kMaxEdges = CUPC_STATIC_MAX_EDGES;
 constexpr uint32_t kMaxKeys = 64 * 8;
 constexpr size_t kAlignS = 256;
 constexpr size_t align_s(size_t x) { return (x + kAlignS - 1) / kAlignS * kAlignS; }
-constexpr size_t kMaxItems = 2ull * kMaxEdges / kMinItemRecords + (kMaxV < 2ull * kMaxEdges ? kMaxV : 2ull * kMaxEdges) + 1;
+constexpr size_t kMaxItems = 4ull * kMaxEdges / kMinItemRecords + (kMaxV < 2ull * kMaxEdges ? kMaxV : 2ull * kMaxEdges) + 1;
 // byte offsets inside the static scratch
 constexpr size_t kOffGc = 0;
 constexpr size_t kOffKeys = align_s(kOffGc + GC_SLOTS * sizeof(uint32_t));
 constexpr size_t kOffCnt = align_s(kOffKeys + kMaxKeys * sizeof(uint64_t));
 constexpr size_t kOffCursor = align_s(kOffCnt + kMaxV * sizeof(uint32_t));
 constexpr size_t kOffRec = align_s(kOffCursor + kMaxV * sizeof(uint32_t));
-constexpr size_t kOffItems = align_s(kOffRec + 2ull * kMaxEdges * sizeof(uint64_t));
+constexpr size_t kOffRecw = align_s(kOffRec + 2ull * kMaxEdges * sizeof(uint64_t));
+constexpr size_t kOffItems = align_s(kOffRecw + 2ull * kMaxEdges * sizeof(uint32_t));
 constexpr size_t kScratchBytes = align_s(kOffItems + kMaxItems * sizeof(uint4));
 
 // Shared by every call on a device, kept between calls.
@@ -106,7 +107,8 @@ extern "C" cupc_status cupc_update_sketch_static(void* sketch, uint32_t V, uint6
   g.R = g.D < kSmemRows ? g.D : kSmemRows;
   g.item_records = kItemRecords;
   g.apply_threads = (int)(((g.L * g.P) + 31) / 32 * 32);
-  g.apply_smem = (int)((size_t)(g.item_records + g.R * g.apply_threads) * sizeof(ulonglong2));
+  g.apply_smem = (int)((size_t)(g.item_records + g.R * g.apply_threads) * sizeof(ulonglong2) +
+                       (size_t)g.item_records * sizeof(uint32_t));
   // the set-up sized the launch for the widest graph; a narrower one fits
   g.apply_grid = ds->apply_grid;
   g.prof_on = false;
@@ -116,6 +118,7 @@ extern "C" cupc_status cupc_update_sketch_static(void* sketch, uint32_t V, uint6
   g.cnt = (uint32_t*)(ds->scratch + kOffCnt);
   g.cursor = (uint32_t*)(ds->scratch + kOffCursor);
   g.rec = (uint64_t*)(ds->scratch + kOffRec);
+  g.recw = (uint32_t*)(ds->scratch + kOffRecw);
   g.items = (uint4*)(ds->scratch + kOffItems);
 
   // the array keeps the previous call's contents: clear what must start at 0

@@ -43,7 +43,8 @@ struct RecArgs {
 // waits until all CTAs of this barrier have arrived. The wait is bounded:
 // after kWaitLimitNs it records kErrTimeout and returns false in every
 // thread of the CTA, which must then return.
-__device__ __forceinline__ bool grid_barrier(uint32_t* gc, uint32_t nblocks, uint32_t& epoch, int* s_ok) {
+__device__ __forceinline__ bool grid_barrier(uint32_t* gc, uint32_t nblocks, uint32_t& epoch, int* s_ok,
+                                             uint64_t limit_ns = kWaitLimitNs) {
   __syncthreads();
   if (threadIdx.x == 0) {
     epoch += 1;
@@ -61,7 +62,7 @@ __device__ __forceinline__ bool grid_barrier(uint32_t* gc, uint32_t nblocks, uin
           ok = 0;
           break;
         }
-        if (t - t0 > kWaitLimitNs) {
+        if (t - t0 > limit_ns) {
           atomicOr(&gc[GC_ERR], kErrTimeout);
           ok = 0;
           break;
@@ -547,6 +548,17 @@ __global__ void __launch_bounds__(kRecThreads, 2) k_recover(RecArgs a) {
 #undef CUPC_GRID_SYNC
 }
 
+// Self-test of the bounded waits: every CTA but `absent` meets at two grid
+// barriers; `absent` returns at once, so the others give up after limit_ns
+// and record kErrTimeout.
+__global__ void k_wait_selftest(uint32_t* gc, uint32_t absent, uint64_t limit_ns) {
+  __shared__ int s_ok;
+  uint32_t epoch = 0;
+  if (blockIdx.x == absent) return;
+  if (!grid_barrier(gc, gridDim.x, epoch, &s_ok, limit_ns)) return;
+  grid_barrier(gc, gridDim.x, epoch, &s_ok, limit_ns);
+}
+
 cudaError_t setup_recover(cupc_graph* g) {
   int per_sm = 0;
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_recover, kRecThreads, 0);
@@ -595,6 +607,35 @@ cudaError_t launch_recover(cupc_graph* g, cudaStream_t s) {
   void* args[] = {&a};
   return cudaLaunchCooperativeKernel((const void*)k_recover, dim3(g->rec_grid), dim3(kRecThreads), args, 0, s);
 }
+
+}  // namespace cupc
+
+extern "C" cupc_status cupc_selftest_wait_timeout(uint32_t ctas, uint32_t limit_us, int absent_cta,
+                                                  cupc_stream stream) {
+  using namespace cupc;
+  if (ctas < 2 || ctas > 64 || limit_us == 0 || limit_us > 1000000) return CUPC_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  uint32_t* gc = nullptr;
+  if (cudaMalloc((void**)&gc, GC_SLOTS * sizeof(uint32_t)) != cudaSuccess) return CUPC_ENOMEM;
+  cupc_status st = CUPC_OK;
+  uint32_t h[GC_SLOTS];
+  uint32_t absent = absent_cta < 0 ? 0xFFFFFFFFu : (uint32_t)absent_cta;
+  uint64_t limit = (uint64_t)limit_us * 1000;
+  void* args[] = {&gc, &absent, &limit};
+  if (cudaMemsetAsync(gc, 0, GC_SLOTS * sizeof(uint32_t), s) != cudaSuccess ||
+      cudaLaunchCooperativeKernel((const void*)k_wait_selftest, dim3(ctas), dim3(32), args, 0, s) != cudaSuccess ||
+      cudaMemcpyAsync(h, gc, sizeof(h), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess) {
+    cudaGetLastError();
+    st = CUPC_ECUDA;
+  } else if (h[GC_ERR] & kErrTimeout) {
+    st = CUPC_ETIMEOUT;
+  }
+  cudaFree(gc);
+  return st;
+}
+
+namespace cupc {
 
 // ---- Connected(u,v) from the recovered labels (Problem 2)
 __global__ void k_query(const uint32_t* __restrict__ pairs, size_t m, uint8_t* __restrict__ out,

@@ -58,62 +58,36 @@ __global__ void k_count(const uint32_t* __restrict__ edges, size_t n, uint32_t* 
   }
 }
 
-// Exclusive scan of the per-vertex record counts into cursors, and the work
-// item list: vertex w with n_w records yields ceil(n_w / kItemRecords) items
-// {w, begin, end, exclusive}; exclusive = the vertex has a single item, so
-// its write-back needs no atomics. Resets cnt for the next chunk.
+// Cursors and work items of one chunk (plan_vertices), single CTA. Resets
+// cnt for the next chunk.
 __global__ void __launch_bounds__(1024) k_plan(uint32_t* cnt, uint32_t* cursor, uint4* items, uint32_t V,
                                                  uint32_t item_records, uint32_t* gc) {
-  __shared__ uint32_t sa[32], sb[32];
   if (ld_cg(&gc[GC_ERR]) & kErrInval) return;
-  uint32_t carry_rec = 0, carry_item = 0;
-  for (uint32_t base = 0; base < V; base += 4 * blockDim.x) {
-    uint32_t w0 = base + 4 * threadIdx.x;
-    uint32_t c[4], ni[4], lr = 0, li = 0;
-#pragma unroll
-    for (int k = 0; k < 4; k++) {
-      c[k] = (w0 + k < V) ? cnt[w0 + k] : 0;
-      ni[k] = (c[k] + item_records - 1) / item_records;
-      lr += c[k];
-      li += ni[k];
-    }
-    uint32_t er, ei, tr, ti;
-    block_scan2(lr, li, er, ei, tr, ti, sa, sb);
-    uint32_t pr = carry_rec + er, pi = carry_item + ei;
-#pragma unroll
-    for (int k = 0; k < 4; k++) {
-      uint32_t w = w0 + k;
-      if (w < V) {
-        cursor[w] = pr;
-        cnt[w] = 0;
-        for (uint32_t q = 0; q < ni[k]; q++) {
-          uint32_t b = pr + q * item_records;
-          uint32_t e = min(pr + c[k], b + item_records);
-          items[pi + q] = make_uint4(w, b, e, ni[k] == 1 ? 1u : 0u);
-        }
-      }
-      pr += c[k];
-      pi += ni[k];
-    }
-    carry_rec += tr;
-    carry_item += ti;
-  }
+  uint32_t nd = 0;
+  const uint32_t nitems = plan_vertices(cnt, cursor, items, V, item_records, &nd);
   if (threadIdx.x == 0) {
-    gc[GC_NITEMS] = carry_item;
+    gc[GC_NITEMS] = nitems;
+    gc[GC_NDIRECT] = nd;
     gc[GC_NEXT_ITEM] = 0;
     gc[GC_BATCHES] += 1;
   }
 }
 
+// Endpoint records grouped by vertex; records of direct-path vertices (the
+// first nd positions) also note their vertex.
 __global__ void k_scatter(const uint32_t* __restrict__ edges, size_t n, uint32_t V, uint32_t* cursor,
-                          uint64_t* __restrict__ rec, const uint32_t* gc) {
+                          uint64_t* __restrict__ rec, uint32_t* __restrict__ recw, const uint32_t* gc) {
   if (ld_cg(&gc[GC_ERR]) & kErrInval) return;
+  const uint32_t nd = ld_cg(&gc[GC_NDIRECT]);
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
     uint32_t u = edges[2 * i], v = edges[2 * i + 1];
     uint32_t a = min(u, v), b = max(u, v);
     uint64_t idx = (uint64_t)a * V + b;
-    rec[atomicAdd(&cursor[u], 1u)] = idx;
-    rec[atomicAdd(&cursor[v], 1u)] = idx;
+    const uint32_t pu = atomicAdd(&cursor[u], 1u), pv = atomicAdd(&cursor[v], 1u);
+    rec[pu] = idx;
+    rec[pv] = idx;
+    if (pu < nd) recw[pu] = u;
+    if (pv < nd) recw[pv] = v;
   }
 }
 
@@ -121,12 +95,13 @@ __global__ void k_scatter(const uint32_t* __restrict__ edges, size_t n, uint32_t
 // apply_item); persistent CTAs pull work items from a counter.
 template <bool kWide>
 __global__ void k_apply(ulonglong2* __restrict__ sketch, const uint64_t* __restrict__ keys,
-                        const uint64_t* __restrict__ rec, const uint4* __restrict__ items, uint32_t* gc,
-                        uint32_t V, uint32_t L, uint32_t C, uint32_t D, uint32_t W, uint32_t P, uint32_t R,
-                        uint32_t item_records) {
+                        const uint64_t* __restrict__ rec, const uint32_t* __restrict__ recw,
+                        const uint4* __restrict__ items, uint32_t* gc, uint32_t V, uint32_t L, uint32_t C,
+                        uint32_t D, uint32_t W, uint32_t P, uint32_t R, uint32_t item_records) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   ulonglong2* s_xp = reinterpret_cast<ulonglong2*>(smem_raw);  // {idx, pre(idx)}
   ulonglong2* s_acc = s_xp + item_records;
+  uint32_t* s_w = reinterpret_cast<uint32_t*>(s_acc + (size_t)R * blockDim.x);
   __shared__ uint32_t s_item;
 
   if (ld_cg(&gc[GC_ERR]) & kErrInval) return;
@@ -142,6 +117,10 @@ __global__ void k_apply(ulonglong2* __restrict__ sketch, const uint64_t* __restr
     const uint32_t it = s_item;
     if (it >= nitems) break;
     const uint4 item = items[it];
+    if (item.x == kDirectItem) {
+      apply_direct<kWide>(l, sketch, V, W, rec + item.y, recw + item.y, item.z - item.y, D, s_xp, s_w);
+      continue;
+    }
     ulonglong2* gb = sketch + ((size_t)l.layer * V + item.x) * W + l.jbase;
     apply_item<kWide>(l, gb, rec + item.y, item.z - item.y, item.w != 0, D, R, s_xp, my_rows, rs);
   }
@@ -175,7 +154,8 @@ cudaError_t setup_update(cupc_graph* g) {
 
 // Shared memory and persistent grid of k_apply for the current tunables.
 cudaError_t configure_apply(cupc_graph* g) {
-  g->apply_smem = (int)((size_t)(g->item_records + g->R * g->apply_threads) * sizeof(ulonglong2));
+  g->apply_smem = (int)((size_t)(g->item_records + g->R * g->apply_threads) * sizeof(ulonglong2) +
+                        (size_t)g->item_records * sizeof(uint32_t));
   cudaError_t e = raise_apply_smem_limit(g->apply_smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
@@ -195,13 +175,13 @@ cudaError_t launch_update_chunk(cupc_graph* g, const uint32_t* edges, size_t n, 
     ProfScope ps(g, s, PC_GROUP, 3);
     k_count<<<grid, 256, 0, s>>>(edges, n, g->cnt, g->gc);
     k_plan<<<1, 1024, 0, s>>>(g->cnt, g->cursor, g->items, g->V, g->item_records, g->gc);
-    k_scatter<<<grid, 256, 0, s>>>(edges, n, g->V, g->cursor, g->rec, g->gc);
+    k_scatter<<<grid, 256, 0, s>>>(edges, n, g->V, g->cursor, g->rec, g->recw, g->gc);
   }
   ProfScope ps(g, s, PC_APPLY, 1);
   int agrid = (int)std::min<size_t>((size_t)g->apply_grid, 2 * n);
   auto kern = g->D > 32 ? k_apply<true> : k_apply<false>;
-  kern<<<agrid, g->apply_threads, g->apply_smem, s>>>(g->sketch, g->keys, g->rec, g->items, g->gc, g->V, g->L, g->C,
-                                                       g->D, g->W, g->P, g->R, g->item_records);
+  kern<<<agrid, g->apply_threads, g->apply_smem, s>>>(g->sketch, g->keys, g->rec, g->recw, g->items, g->gc, g->V,
+                                                       g->L, g->C, g->D, g->W, g->P, g->R, g->item_records);
   return cudaGetLastError();
 }
 

@@ -6,46 +6,124 @@
 
 namespace cupc {
 
-// Block-wide exclusive scan of two u32 values per thread (1024 threads).
-__device__ __forceinline__ void block_scan2(uint32_t a, uint32_t b, uint32_t& ea, uint32_t& eb, uint32_t& ta,
-                                            uint32_t& tb, uint32_t* sa, uint32_t* sb) {
+// Block-wide exclusive scan of three u32 values per thread (any multiple of
+// 32 threads up to 1024). e* = exclusive prefix, t* = block totals.
+__device__ __forceinline__ void block_scan3(const uint32_t (&v)[3], uint32_t (&e)[3], uint32_t (&t)[3],
+                                            uint32_t (*sw)[32]) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  uint32_t ia = a, ib = b;
+  uint32_t inc[3] = {v[0], v[1], v[2]};
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
-    uint32_t xa = __shfl_up_sync(0xffffffffu, ia, o), xb = __shfl_up_sync(0xffffffffu, ib, o);
-    if (lane >= o) {
-      ia += xa;
-      ib += xb;
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+      const uint32_t x = __shfl_up_sync(0xffffffffu, inc[k], o);
+      if (lane >= o) inc[k] += x;
     }
   }
-  if (lane == 31) {
-    sa[wid] = ia;
-    sb[wid] = ib;
-  }
+  if (lane == 31)
+#pragma unroll
+    for (int k = 0; k < 3; k++) sw[k][wid] = inc[k];
   __syncthreads();
   if (wid == 0) {
-    uint32_t va = lane < nw ? sa[lane] : 0, vb = lane < nw ? sb[lane] : 0;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      uint32_t xa = __shfl_up_sync(0xffffffffu, va, o), xb = __shfl_up_sync(0xffffffffu, vb, o);
-      if (lane >= o) {
-        va += xa;
-        vb += xb;
+    for (int k = 0; k < 3; k++) {
+      uint32_t x = lane < nw ? sw[k][lane] : 0;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
       }
-    }
-    if (lane < nw) {
-      sa[lane] = va;
-      sb[lane] = vb;
+      if (lane < nw) sw[k][lane] = x;
     }
   }
   __syncthreads();
-  uint32_t wa = wid ? sa[wid - 1] : 0, wb = wid ? sb[wid - 1] : 0;
-  ea = wa + ia - a;
-  eb = wb + ib - b;
-  ta = sa[nw - 1];
-  tb = sb[nw - 1];
+#pragma unroll
+  for (int k = 0; k < 3; k++) {
+    e[k] = (wid ? sw[k][wid - 1] : 0) + inc[k] - v[k];
+    t[k] = sw[k][nw - 1];
+  }
   __syncthreads();
+}
+
+// Vertices with at most this many endpoint records in a batch take the
+// direct path: no shared-memory fold, each record's buckets are XORed
+// straight into HBM with fire-and-forget atomics.
+constexpr uint32_t kDirectMax = 2;
+// Work item whose records belong to several direct-path vertices, and its
+// size: small, so that a sparse batch still spreads over every SM.
+constexpr uint32_t kDirectItem = 0xFFFFFFFFu;
+constexpr uint32_t kDirectItemRecords = 64;
+
+// Work plan of one batch, run by one CTA: vertices with more than
+// kDirectMax records ("fold" vertices) get record segments after all direct
+// records and ceil(n_w / item_records) items {w, begin, end, exclusive}
+// (exclusive: the vertex has a single item, so its write-back needs no
+// atomics); direct vertices' records come first and are cut into items of
+// item_records records {kDirectItem, begin, end, 0}. Writes the per-vertex
+// scatter cursors, resets cnt, returns the item count and the number of
+// direct records (*nd). Direct items hold kDirectItemRecords records.
+__device__ __forceinline__ uint32_t plan_vertices(uint32_t* cnt, uint32_t* cursor, uint4* items, uint32_t V,
+                                                  uint32_t item_records, uint32_t* nd_out) {
+  __shared__ uint32_t sw[3][32];
+  __shared__ uint32_t s_nd;
+  // pass 1: how many records go the direct way
+  uint32_t dsum = 0;
+  for (uint32_t w = threadIdx.x; w < V; w += blockDim.x) {
+    const uint32_t c = cnt[w];
+    dsum += c <= kDirectMax ? c : 0;
+  }
+  dsum = __reduce_add_sync(0xffffffffu, dsum);
+  if (threadIdx.x == 0) s_nd = 0;
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) atomicAdd(&s_nd, dsum);
+  __syncthreads();
+  const uint32_t nd = s_nd;
+  // pass 2: cursors and fold items
+  uint32_t carry[3] = {0, 0, 0};  // fold records, direct records, fold items
+  for (uint32_t base = 0; base < V; base += 4 * blockDim.x) {
+    const uint32_t w0 = base + 4 * threadIdx.x;
+    uint32_t c[4], v[3] = {0, 0, 0};
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      c[k] = (w0 + k < V) ? cnt[w0 + k] : 0;
+      if (c[k] > kDirectMax) {
+        v[0] += c[k];
+        v[2] += (c[k] + item_records - 1) / item_records;
+      } else {
+        v[1] += c[k];
+      }
+    }
+    uint32_t e[3], t[3];
+    block_scan3(v, e, t, sw);
+    uint32_t pf = nd + carry[0] + e[0], pd = carry[1] + e[1], pi = carry[2] + e[2];
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      const uint32_t w = w0 + k;
+      if (w >= V) continue;
+      cnt[w] = 0;
+      if (c[k] > kDirectMax) {
+        const uint32_t ni = (c[k] + item_records - 1) / item_records;
+        cursor[w] = pf;
+        for (uint32_t q = 0; q < ni; q++) {
+          const uint32_t b = pf + q * item_records;
+          items[pi + q] = make_uint4(w, b, min(pf + c[k], b + item_records), ni == 1 ? 1u : 0u);
+        }
+        pf += c[k];
+        pi += ni;
+      } else {
+        cursor[w] = pd;
+        pd += c[k];
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 3; k++) carry[k] += t[k];
+  }
+  // direct items after the fold items
+  const uint32_t nfold = carry[2], ndi = (nd + kDirectItemRecords - 1) / kDirectItemRecords;
+  for (uint32_t q = threadIdx.x; q < ndi; q += blockDim.x)
+    items[nfold + q] = make_uint4(kDirectItem, q * kDirectItemRecords, min(nd, (q + 1) * kDirectItemRecords), 0u);
+  *nd_out = nd;
+  return nfold + ndi;
 }
 
 __device__ __forceinline__ void xor_bucket_atomic(ulonglong2* p, ulonglong2 v) {
@@ -210,6 +288,41 @@ __device__ __forceinline__ void apply_item(const ApplyLane& l, ulonglong2* gb, c
     }
   } else {
     my_rows[0] = make_ulonglong2(0, 0);
+  }
+  __syncthreads();
+}
+
+
+// Direct-path item: records of several vertices, each record's buckets XORed
+// straight into HBM (atomics, no write-back). recw[i] is record i's vertex.
+template <bool kWide>
+__device__ __forceinline__ void apply_direct(const ApplyLane& l, ulonglong2* sketch, uint32_t V, uint32_t W,
+                                             const uint64_t* __restrict__ rec, const uint32_t* __restrict__ recw,
+                                             uint32_t n, uint32_t D, ulonglong2* s_xp, uint32_t* s_w) {
+  const uint32_t tid = threadIdx.x;
+  for (uint32_t i = tid; i < n; i += blockDim.x) {
+    const uint64_t x = rec[i];
+    s_xp[i] = make_ulonglong2(x, pre_mix(x));
+    s_w[i] = recw[i];
+  }
+  __syncthreads();
+  ulonglong2* lbase = sketch + (size_t)l.layer * V * W + l.jbase;
+  for (uint32_t i0 = 0; i0 < n; i0 += 4) {
+    ulonglong2 x[4];
+    uint64_t h[4], g[4];
+#pragma unroll
+    for (uint32_t k = 0; k < 4; k++) {
+      x[k] = s_xp[min(i0 + k, n - 1)];
+      h[k] = mix_tail(x[k].y ^ l.kpre);
+    }
+#pragma unroll
+    for (uint32_t k = 0; k < 4; k++) g[k] = __shfl_sync(0xffffffffu, h[k], l.chk_lane);
+#pragma unroll
+    for (uint32_t k = 0; k < 4; k++) {
+      uint32_t d = depth_fast<kWide>(h[k], D);
+      if (l.row0) d = 0;
+      if (l.active && i0 + k < n) xor_bucket_atomic(lbase + (size_t)s_w[i0 + k] * W + d, make_ulonglong2(x[k].x, g[k]));
+    }
   }
   __syncthreads();
 }

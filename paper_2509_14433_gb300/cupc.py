@@ -63,6 +63,7 @@ _SIGS = {
     "cupc_profile_read": (ctypes.c_int, [_P, _P, _P, _sz]),
     "cupc_destroy": (None, [_P]),
     "cupc_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "cupc_selftest_wait_timeout": (ctypes.c_int, [_u32, _u32, ctypes.c_int, _P]),
     "cupc_update_sketch_static": (ctypes.c_int, [_P, _u32, _u64, _P, _P, _sz, _P, _P]),
 }
 for _name, (_res, _args) in _SIGS.items():
@@ -263,6 +264,10 @@ def cupc_profile_read(g, ms, launches, n: int) -> int:
 
 def cupc_destroy(g) -> None:
     _lib.cupc_destroy(g)
+
+
+def cupc_selftest_wait_timeout(ctas: int, limit_us: int, absent_cta: int, stream=None) -> int:
+    return _lib.cupc_selftest_wait_timeout(ctas, limit_us, absent_cta, stream_handle(stream))
 
 
 def cupc_status_string(st: int) -> str:

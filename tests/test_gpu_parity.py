@@ -284,3 +284,21 @@ def test_smaller_graph_does_not_shrink_an_earlier_graphs_launch():
     assert dev_big.sync() == 0
     assert np.array_equal(dev_big.export(), ref.export())
     assert_same_recovery(dev_big, ref)
+
+
+def test_bounded_device_wait_reports_timeout_and_context_survives():
+    # one CTA never reaches the grid barrier: the others give up after the
+    # limit, report CUPC_ETIMEOUT, and the context keeps working
+    from paper_2509_14433_gb300 import cupc as C
+    import time
+    t = time.perf_counter()
+    assert C.cupc_selftest_wait_timeout(8, 20000, 3) == C.CUPC_ETIMEOUT
+    assert time.perf_counter() - t < 5.0
+    assert C.cupc_selftest_wait_timeout(8, 20000, -1) == C.CUPC_OK
+    V = 50
+    dev, ref = _dev(V, 1), O.Graph(V, 1)
+    E = WL.er_edges(V, 0.1, 2)
+    dev.update(E)
+    ref.update(E)
+    assert np.array_equal(dev.export(), ref.export())
+    assert C.cupc_selftest_wait_timeout(1, 100, -1) == C.CUPC_EINVAL
