@@ -43,6 +43,24 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
+def max_over_ranks(value: float, device=None) -> float:
+    """The slowest rank's value (all ranks must call it); the value itself on
+    a single process."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return value
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_step: int, steps: int, world: int, max_ms: float) -> float:
+    """Weak scaling: every rank processes units_per_step per step; the job's
+    rate is all ranks' units over the slowest rank's time."""
+    return units_per_step * steps * world / (max_ms / 1e3)
+
+
 def make_dense_stream():
     E, n_del, order = WL.dense_stream(V=V_DENSE, p=P_DENSE, batch=BATCH, delete_frac=0.1, seed=SEED)
     return E, E[order[:n_del]]
@@ -225,12 +243,9 @@ def run_gpu(args):
     C.cupc_profile_enable(g, 0)
     ms = ev0.elapsed_time(ev1)
     barrier()
-    if pg is not None:
-        t = torch.tensor([ms], device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dev)
     upd_per_step = nE + nD
-    value = upd_per_step * args.steps * world / (ms / 1e3)
+    value = whole_job_rate(upd_per_step, args.steps, world, ms)
     assert C.cupc_sync(g, stream) == C.CUPC_OK
 
     # ---- e2e: the same job through the C-ABI with pinned host buffers
@@ -260,7 +275,8 @@ def run_gpu(args):
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     barrier()
-    e2e_val = upd_per_step * e2e_steps * world / e2e_s
+    e2e_s = max_over_ranks(e2e_s, dev)
+    e2e_val = whole_job_rate(upd_per_step, e2e_steps, world, e2e_s * 1e3)
     assert nf_h == nf and torch.equal(forest_h[:nf], forest_d[:nf].cpu())
 
     # ---- Connected-query latency right after a dense update batch

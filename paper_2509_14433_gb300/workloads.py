@@ -158,7 +158,7 @@ class RmatStream:
         self.gen = torch.Generator(device=self.device).manual_seed(seed)
         nbits = self.V * self.V
         self.bitmap = torch.zeros((nbits + 63) // 64, dtype=torch.int64, device=self.device)
-        self.inserted = []  # append-only id tensors
+        self.pool = torch.zeros(1 << 20, dtype=torch.int64, device=self.device)  # inserted ids, append-only
         self.n_inserted = 0
         self.fallbacks = 0
 
@@ -182,55 +182,63 @@ class RmatStream:
         x = t.rand(1, generator=self.gen, device=self.device).item()
         return int(np.exp(np.log(self.lo) + x * (np.log(self.hi) - np.log(self.lo))))
 
+    def _take(self, cand, want_bit, need):
+        """Up to `need` ids of `cand` whose presence bit is `want_bit`, first
+        occurrences only, in draw order; their bits are flipped at once, so
+        later draws of the same batch see them as taken."""
+        cand = cand[self._bits(cand) == want_bit]
+        cand = cand[self._unique_keep(cand)][:need]
+        self._flip(cand, 1 if want_bit == 0 else -1)
+        return cand
+
     def _deletes(self, k):
         t = self.torch
         if k == 0 or self.n_inserted == 0:
             return t.zeros(0, dtype=t.int64, device=self.device)
-        pool = t.cat(self.inserted) if len(self.inserted) > 1 else self.inserted[0]
-        self.inserted = [pool]
-        got = t.zeros(0, dtype=t.int64, device=self.device)
+        pool = self.pool[:self.n_inserted]
+        parts, have = [], 0
         for _ in range(64):
-            need = k - got.numel()
+            need = k - have
             if need <= 0:
                 break
             pos = t.randint(0, pool.numel(), (2 * need + 16,), generator=self.gen, device=self.device)
-            ids = pool[pos]
-            ids = ids[self._bits(ids) == 1]
-            ids = t.cat([got, ids])
-            ids = ids[self._unique_keep(ids)]
-            got = ids[:k]
-        self._flip(got, -1)
-        return got
+            got = self._take(pool[pos], 1, need)
+            parts.append(got)
+            have += got.numel()
+        return t.cat(parts) if parts else t.zeros(0, dtype=t.int64, device=self.device)
 
     def _inserts(self, k):
         t = self.torch
-        got = t.zeros(0, dtype=t.int64, device=self.device)
+        parts, have = [], 0
         for _ in range(64):
-            need = k - got.numel()
+            need = k - have
             if need <= 0:
                 break
             u, v = rmat_pairs(need, self.levels, self.probs, self.gen, self.device)
             ok = u != v
-            a, b = t.minimum(u, v)[ok], t.maximum(u, v)[ok]
-            ids = a * self.V + b
-            ids = ids[self._bits(ids) == 0]
-            ids = t.cat([got, ids])
-            got = ids[self._unique_keep(ids)]
-        while got.numel() < k:  # uniform absent pairs
-            need = k - got.numel()
+            got = self._take(t.minimum(u, v)[ok] * self.V + t.maximum(u, v)[ok], 0, need)
+            parts.append(got)
+            have += got.numel()
+        while have < k:  # uniform absent pairs
+            need = k - have
             u = t.randint(0, self.V, (need,), generator=self.gen, device=self.device)
             v = t.randint(0, self.V, (need,), generator=self.gen, device=self.device)
             ok = u != v
-            ids = t.minimum(u, v)[ok] * self.V + t.maximum(u, v)[ok]
-            ids = ids[self._bits(ids) == 0]
-            before = got.numel()
-            got = t.cat([got, ids])
-            got = got[self._unique_keep(got)]
-            self.fallbacks += got.numel() - before
-        got = got[:k]
-        self._flip(got, 1)
-        self.inserted.append(got)
-        self.n_inserted += got.numel()
+            got = self._take(t.minimum(u, v)[ok] * self.V + t.maximum(u, v)[ok], 0, need)
+            parts.append(got)
+            have += got.numel()
+            self.fallbacks += got.numel()
+        got = t.cat(parts) if parts else t.zeros(0, dtype=t.int64, device=self.device)
+        need = self.n_inserted + got.numel()
+        if need > self.pool.numel():
+            cap = self.pool.numel()
+            while cap < need:
+                cap *= 2
+            grown = t.zeros(cap, dtype=t.int64, device=self.device)
+            grown[:self.n_inserted] = self.pool[:self.n_inserted]
+            self.pool = grown
+        self.pool[self.n_inserted:need] = got
+        self.n_inserted = need
         return got
 
     def next_batch(self, size: int | None = None):

@@ -1,0 +1,50 @@
+"""The seeded input generators produce valid streams (Problem 1 asks that an
+insert names an absent edge and a delete a present one): every batch is
+replayed against a set of present edges, update by update."""
+import numpy as np
+
+from paper_2509_14433_gb300 import workloads as WL
+
+
+def _replay(batches, V):
+    present = set()
+    for E, ops in batches:
+        for (u, v), o in zip(np.asarray(E).tolist(), np.asarray(ops).tolist()):
+            assert 0 <= u < v < V
+            i = u * V + v
+            if o == 1:
+                assert i not in present
+                present.add(i)
+            else:
+                assert o == -1 and i in present
+                present.remove(i)
+    return present
+
+
+def test_rmat_stream_is_valid_and_bitmap_tracks_it():
+    s = WL.RmatStream(levels=9, seed=5, batch_lo=50, batch_hi=4000)
+    batches = [tuple(x.numpy() for x in s.next_batch()) for _ in range(60)]
+    sizes = [len(o) for _, o in batches]
+    assert min(sizes) >= 50 and max(sizes) <= 4000
+    # 20% of each batch after the first deletes, deletes first
+    for _, o in batches[1:]:
+        k = int(np.sum(o == -1))
+        assert abs(k - 0.2 * len(o)) <= 1
+        assert np.all(o[:k] == -1) and np.all(o[k:] == 1)
+    present = _replay(batches, s.V)
+    bits = np.unpackbits(s.bitmap.numpy().view(np.uint8), bitorder="little")
+    assert set(np.nonzero(bits)[0].tolist()) == present
+
+
+def test_toggle_and_dense_streams_are_valid():
+    V = 300
+    steps = WL.plain_stream(V=V, p=0.3, n_toggles=20000, query_every=5000, query_size=10, seed=2)
+    ups = [(st[1], st[2]) for st in steps if st[0] == "update"]
+    assert sum(st[0] == "query" for st in steps) == 4
+    present = _replay(ups, V)
+    assert present == set(int(x) for x in WL.final_edge_set(V, steps))
+    Ed, n_del, order = WL.dense_stream(V=V, p=0.5, seed=3)
+    assert abs(len(Ed) - 0.5 * V * (V - 1) / 2) < 5 * np.sqrt(V * V / 8)
+    dels = Ed[order[:n_del]]
+    assert n_del == round(0.1 * len(Ed))
+    _replay([(Ed, np.ones(len(Ed), np.int8)), (dels, -np.ones(len(dels), np.int8))], V)
