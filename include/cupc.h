@@ -225,7 +225,7 @@ void cupc_server_destroy(cupc_server* s);
 
 /* Launch tunables of the update's apply kernel (results are identical for
  * every setting; only speed changes): item_records = endpoint records per
- * work item (64..512, 0 = 512), smem_rows = rows per column folded in shared
+ * work item (64..512, 0 = 256), smem_rows = rows per column folded in shared
  * memory (1..min(D, 16), 0 = min(D, 8)); deeper rows go straight to HBM),
  * ctas_per_sm = resident CTAs per SM of the persistent grid (0 = as many as
  * fit). CUPC_EINVAL (previous settings kept) when out of range.

@@ -24,7 +24,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 DEFAULT_CACHE = os.path.join(HERE, "tuning_gb300.json")
 
-ITEM_RECORDS = (128, 256, 512)
+ITEM_RECORDS = (64, 128, 256, 512)
 SMEM_ROWS = (8, 12, 16)
 CTAS_PER_SM = (0, 2)
 
@@ -130,7 +130,7 @@ def tune(V: int, sizes=None, reps: int = 3, seed: int = 1, path: str = DEFAULT_C
                             results.append((t, (it, rows, cps)))
             results.sort()
             best_t, best = results[0]
-            default = [t for t, s in results if s == (512, min(8, D), 0)]
+            default = [t for t, s in results if s == (256, min(8, D), 0)]
             ent[str(bucket_of(n))] = {"setting": list(best), "apply_ms": best_t,
                                       "default_ms": default[0] if default else None, "edges": n}
             if verbose:

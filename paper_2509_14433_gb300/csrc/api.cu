@@ -437,7 +437,7 @@ cupc_status cupc_profile_read(cupc_graph* g, double* ms, uint64_t* launches, siz
 
 cupc_status cupc_set_tuning(cupc_graph* g, uint32_t item_records, uint32_t smem_rows, uint32_t ctas_per_sm) {
   if (!g) return CUPC_EINVAL;
-  if (item_records == 0) item_records = kItemRecords;
+  if (item_records == 0) item_records = kDefaultItemRecords;
   if (smem_rows == 0) smem_rows = g->D < kSmemRows ? g->D : kSmemRows;
   if (item_records < kMinItemRecords || item_records > kItemRecords || smem_rows > kSmemRowsMax || smem_rows > g->D)
     return CUPC_EINVAL;

@@ -256,7 +256,7 @@ cudaError_t get_exec(cupc_batcher* b, uint32_t threads, uint32_t rmax, uint32_t 
   x.threads = threads;
   x.rmax = rmax;
   x.imax = imax;
-  x.apply_smem = (int)((size_t)(imax + rmax * threads) * sizeof(ulonglong2) + (size_t)imax * sizeof(uint32_t));
+  x.apply_smem = (int)apply_smem_bytes(imax, rmax, threads);
   cudaFuncAttributes fa;
   cudaError_t e = cudaFuncGetAttributes(&fa, k_apply_m);
   if (e != cudaSuccess) return e;

@@ -27,8 +27,14 @@ constexpr uint32_t kNoneU32 = 0xFFFFFFFFu;
 constexpr uint32_t kSmemRows = 8;      // default (the autotuner's usual pick on GB300)
 constexpr uint32_t kSmemRowsMax = 16;
 // Records (endpoint incidences) per update work item.
-constexpr uint32_t kItemRecords = 512;  // default and maximum
+constexpr uint32_t kItemRecords = 512;  // maximum
+constexpr uint32_t kDefaultItemRecords = 256;
 constexpr uint32_t kMinItemRecords = 64;
+// Dynamic shared memory of an apply CTA: staged records {idx, pre(idx)},
+// rows x threads fold rows, and the records' vertices (direct path).
+inline size_t apply_smem_bytes(uint32_t item_records, uint32_t rows, uint32_t threads) {
+  return ((size_t)item_records + (size_t)rows * threads) * 16 + (size_t)item_records * 4;
+}
 // Threads of the recovery kernel and members per reduction work item.
 constexpr uint32_t kRecThreads = 256;
 constexpr uint32_t kRecSpan = 8;  // also the largest "small" component

@@ -105,10 +105,9 @@ extern "C" cupc_status cupc_update_sketch_static(void* sketch, uint32_t V, uint6
   g.sms = ds->sms;
   g.P = ds->P;
   g.R = g.D < kSmemRows ? g.D : kSmemRows;
-  g.item_records = kItemRecords;
+  g.item_records = kDefaultItemRecords;
   g.apply_threads = (int)(((g.L * g.P) + 31) / 32 * 32);
-  g.apply_smem = (int)((size_t)(g.item_records + g.R * g.apply_threads) * sizeof(ulonglong2) +
-                       (size_t)g.item_records * sizeof(uint32_t));
+  g.apply_smem = (int)apply_smem_bytes(g.item_records, g.R, (uint32_t)g.apply_threads);
   // the set-up sized the launch for the widest graph; a narrower one fits
   g.apply_grid = ds->apply_grid;
   g.prof_on = false;

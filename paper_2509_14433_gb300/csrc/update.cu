@@ -146,7 +146,7 @@ cudaError_t setup_update(cupc_graph* g) {
   g->P = 1;
   while (g->P < g->C + 1) g->P <<= 1;
   g->R = g->D < kSmemRows ? g->D : kSmemRows;
-  g->item_records = kItemRecords;
+  g->item_records = kDefaultItemRecords;
   g->apply_cps = 0;
   g->apply_threads = (int)(((g->L * g->P) + 31) / 32 * 32);
   return configure_apply(g);
@@ -154,8 +154,7 @@ cudaError_t setup_update(cupc_graph* g) {
 
 // Shared memory and persistent grid of k_apply for the current tunables.
 cudaError_t configure_apply(cupc_graph* g) {
-  g->apply_smem = (int)((size_t)(g->item_records + g->R * g->apply_threads) * sizeof(ulonglong2) +
-                        (size_t)g->item_records * sizeof(uint32_t));
+  g->apply_smem = (int)apply_smem_bytes(g->item_records, g->R, (uint32_t)g->apply_threads);
   cudaError_t e = raise_apply_smem_limit(g->apply_smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
