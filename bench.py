@@ -87,19 +87,31 @@ def expected_touched_buckets(counts, L, C, D):
     return float(L * (mult * (1.0 + C * per_col)).sum())
 
 
-def apply_traffic():
-    """DRAM bytes per k_apply launch from the committed ncu summary, scaled
-    to a 2^20-edge batch; None when the kernel source changed since the
-    counters were taken."""
+def apply_source_digest():
+    """md5 over what defines k_apply: the shared device header, the common
+    header and the kernel's own text in update.cu."""
     import hashlib
+    import re
+    csrc = os.path.join(ROOT, "paper_2509_14433_gb300", "csrc")
+    h = hashlib.md5()
+    for f in ("update_dev.cuh", "common.cuh"):
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    upd = open(os.path.join(csrc, "update.cu")).read()
+    m = re.search(r"__global__ void k_apply\(.*?\n}\n", upd, re.S)
+    h.update((m.group(0) if m else upd).encode())
+    return h.hexdigest()
+
+
+def apply_traffic(setting):
+    """DRAM bytes per k_apply launch from the committed ncu summary; None
+    when the kernel's source or its launch setting changed since the
+    counters were taken."""
     tp = os.path.join(ROOT, "profiles", "k_apply_traffic.json")
-    src = os.path.join(ROOT, "paper_2509_14433_gb300", "csrc", "update.cu")
     try:
         rec = json.load(open(tp))
-        md5 = hashlib.md5(open(src, "rb").read()).hexdigest()
     except (OSError, ValueError):
         return None
-    if rec.get("update_cu_md5") != md5:
+    if rec.get("source_md5") != apply_source_digest() or list(rec.get("setting", [])) != list(setting):
         return None
     return rec.get("bytes_per_launch")
 
@@ -317,7 +329,9 @@ def run_gpu(args):
         pass
     peak = float(peaks.get("hbm_gbs", 6800.0))
     achieved = apply_bytes_per_launch / (apply_ms * 1e-3) / 1e9
-    traffic = apply_traffic()
+    tun = np.zeros(4, np.uint32)
+    C.cupc_get_tuning(g, tun)
+    traffic = apply_traffic([int(x) for x in tun[:3]])
     gpu_launches = int(nl_prof.sum())
     shares = {name: round(float(ms_prof[k]) / max(1e-9, float(ms_prof.sum())), 4)
               for k, name in enumerate(["validate", "group", "apply", "recover", "query", "sort"])}

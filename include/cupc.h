@@ -67,17 +67,21 @@ typedef struct {
                          batches are applied chunk by chunk, which is exact
                          because sketch addition is XOR */
 } cupc_params;
+/* Limits (else CUPC_EINVAL): W = 1 + C*D <= 256; L * P <= 1024 with P the
+ * power of two >= C + 1 (the update kernel runs one thread per layer and
+ * column, plus a checksum thread); 2 * max_batch < 2^32. */
 
 /* Device bytes cupc_init needs for V vertices (sketches + scratch), so that
  * a caller (e.g. a PyTorch allocation) can own the memory. 0 on bad input. */
 size_t cupc_workspace_bytes(uint32_t V, const cupc_params* params /* nullable */);
 
-/* Create a graph on V >= 2 vertices with no edges; hash keys derive from
+/* Create a graph on 2 <= V <= 2^21 vertices with no edges (the recovery packs
+ * an edge id and a vertex id into one 64-bit key); hash keys derive from
  * `seed`. `workspace` (device, >= cupc_workspace_bytes, 256-byte aligned)
  * is borrowed for the graph's lifetime; NULL makes the library allocate.
  * The graph is zeroed on `stream` before the call returns.
- * Errors: CUPC_EINVAL (V < 2, params out of range, misaligned workspace),
- * CUPC_ENOMEM, CUPC_ECUDA. */
+ * Errors: CUPC_EINVAL (V out of range, params out of range, misaligned
+ * workspace), CUPC_ENOMEM, CUPC_ECUDA. */
 cupc_status cupc_init(uint32_t V, uint64_t seed, const cupc_params* params, void* workspace,
                       cupc_stream stream, cupc_graph** out);
 

@@ -31,7 +31,7 @@ struct Dims {
 Dims derive(uint32_t V, const cupc_params* p) {
   Dims d{};
   d.ok = false;
-  if (V < 2) return d;
+  if (V < 2 || V > kMaxVertices) return d;
   uint32_t lg = ceil_log2(V);
   d.V = V;
   d.L = (p && p->rounds) ? p->rounds : lg + 2;
@@ -42,6 +42,9 @@ Dims derive(uint32_t V, const cupc_params* p) {
   if (d.C > 31 || d.D > 63 || d.D < 1 || d.L < 1 || d.L > 64) return d;
   d.W = 1 + d.C * d.D;
   if (d.W > 32 * kWarpBuckets) return d;
+  uint32_t P = 1;  // apply threads per layer: the columns and the checksum lane
+  while (P < d.C + 1) P <<= 1;
+  if (d.L * P > 1024) return d;  // one apply CTA holds every (layer, lane)
   // the edge index u*V+v must fit the 64-bit bucket word; record offsets are u32
   if ((uint64_t)d.max_batch * 2 >= 0xFFFFFFFFull) return d;
   d.ok = true;
@@ -50,9 +53,9 @@ Dims derive(uint32_t V, const cupc_params* p) {
 
 // Byte offsets of every device array inside the workspace.
 struct Layout {
-  size_t sketch, keys, gc, cnt, cursor, rec, recw, items, stage_edges, stage_ops, label, parent, minv, rcnt, roff,
+  size_t sketch, keys, gc, cnt, cursor, rec, recw, items, part, stage_edges, stage_ops, label, parent, minv, rcnt, roff,
       perm, permb, pcount, final_, merged, best, best2, cand, forest, forest_sorted, acc, log_ids, log_live,
-      log_ncand, total;
+      log_ncand, clist, total;
 };
 
 Layout layout(const Dims& d) {
@@ -73,6 +76,7 @@ Layout layout(const Dims& d) {
   l.rec = take(2 * B * 8);
   l.recw = take(2 * B * 4);
   l.items = take(nitems * sizeof(uint4));
+  l.part = take(kPlanSlices * sizeof(uint4));
   l.stage_edges = take(2 * B * 4);
   l.stage_ops = take(B);
   l.label = take(V * 4);
@@ -94,6 +98,7 @@ Layout layout(const Dims& d) {
   l.log_ids = take((size_t)d.L * V * 8);
   l.log_live = take(d.L * 4);
   l.log_ncand = take(d.L * 4);
+  l.clist = take(V * 4);
   l.total = off;
   return l;
 }
@@ -184,6 +189,7 @@ cupc_status cupc_init(uint32_t V, uint64_t seed, const cupc_params* params, void
   g->rec = (uint64_t*)(b + l.rec);
   g->recw = (uint32_t*)(b + l.recw);
   g->items = (uint4*)(b + l.items);
+  g->part = (uint4*)(b + l.part);
   g->stage_edges = (uint32_t*)(b + l.stage_edges);
   g->stage_ops = (int8_t*)(b + l.stage_ops);
   g->stage_pairs = g->stage_edges;
@@ -207,6 +213,7 @@ cupc_status cupc_init(uint32_t V, uint64_t seed, const cupc_params* params, void
   g->log_ids = (uint64_t*)(b + l.log_ids);
   g->log_live = (uint32_t*)(b + l.log_live);
   g->log_ncand = (uint32_t*)(b + l.log_ncand);
+  g->clist = (uint32_t*)(b + l.clist);
   if (setup_update(g) != cudaSuccess || setup_recover(g) != cudaSuccess) {
     cudaGetLastError();
     return fail(CUPC_ECUDA);

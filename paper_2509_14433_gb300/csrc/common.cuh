@@ -21,6 +21,9 @@ constexpr uint32_t kErrTimeout = 2u;
 constexpr uint32_t kErrQuery = 4u;  // a query pair out of range (does not drop updates)
 constexpr uint64_t kNone = ~0ull;
 constexpr uint32_t kNoneU32 = 0xFFFFFFFFu;
+// Most vertices: an edge id (< V^2) and a vertex id share one 64-bit key in
+// the recovery's hook.
+constexpr uint32_t kMaxVertices = 1u << 21;
 
 // Rows per column that the update kernel folds in shared memory; deeper rows
 // (probability 2^-kSmemRows per index) are XORed straight into HBM.
@@ -30,6 +33,8 @@ constexpr uint32_t kSmemRowsMax = 16;
 constexpr uint32_t kItemRecords = 512;  // maximum
 constexpr uint32_t kDefaultItemRecords = 256;
 constexpr uint32_t kMinItemRecords = 64;
+// Most vertex slices of the update's plan kernels.
+constexpr uint32_t kPlanSlices = 1024;
 // Dynamic shared memory of an apply CTA: staged records {idx, pre(idx)},
 // rows x threads fold rows, and the records' vertices (direct path).
 inline size_t apply_smem_bytes(uint32_t item_records, uint32_t rows, uint32_t threads) {
@@ -120,6 +125,7 @@ struct cupc_graph {
   uint64_t* rec;       // 2*max_batch
   uint32_t* recw;      // 2*max_batch: vertex of each direct-path record
   uint4* items;        // 4*max_batch/kMinItemRecords + min(V, 2*max_batch) + 1
+  uint4* part;         // kPlanSlices per-slice totals of the plan
   uint32_t* stage_edges;  // 2*max_batch
   int8_t* stage_ops;      // max_batch
   uint32_t* stage_pairs;  // 2*max_pairs
@@ -144,6 +150,7 @@ struct cupc_graph {
   uint64_t* log_ids; // L*V
   uint32_t* log_live;   // L
   uint32_t* log_ncand;  // L
+  uint32_t* clist;      // V: component of each logged candidate of a round
   cupc_status last_recovery;
   // profiling: (kernel class, start, stop, launches) per recorded launch group
   struct ProfRec {

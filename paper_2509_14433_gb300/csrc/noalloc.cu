@@ -28,7 +28,8 @@ constexpr size_t kOffCursor = align_s(kOffCnt + kMaxV * sizeof(uint32_t));
 constexpr size_t kOffRec = align_s(kOffCursor + kMaxV * sizeof(uint32_t));
 constexpr size_t kOffRecw = align_s(kOffRec + 2ull * kMaxEdges * sizeof(uint64_t));
 constexpr size_t kOffItems = align_s(kOffRecw + 2ull * kMaxEdges * sizeof(uint32_t));
-constexpr size_t kScratchBytes = align_s(kOffItems + kMaxItems * sizeof(uint4));
+constexpr size_t kOffPart = align_s(kOffItems + kMaxItems * sizeof(uint4));
+constexpr size_t kScratchBytes = align_s(kOffPart + kPlanSlices * sizeof(uint4));
 
 // Shared by every call on a device, kept between calls.
 static __device__ __align__(256) unsigned char cupc_static_scratch[kScratchBytes];
@@ -119,6 +120,7 @@ extern "C" cupc_status cupc_update_sketch_static(void* sketch, uint32_t V, uint6
   g.rec = (uint64_t*)(ds->scratch + kOffRec);
   g.recw = (uint32_t*)(ds->scratch + kOffRecw);
   g.items = (uint4*)(ds->scratch + kOffItems);
+  g.part = (uint4*)(ds->scratch + kOffPart);
 
   // the array keeps the previous call's contents: clear what must start at 0
   if (cudaMemsetAsync(g.gc, 0, GC_SLOTS * sizeof(uint32_t), s) != cudaSuccess) return CUPC_ECUDA;

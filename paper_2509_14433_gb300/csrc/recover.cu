@@ -35,6 +35,7 @@ struct RecArgs {
   ulonglong2* cand;  // {edge, label[u] << 32 | label[v]} of a component's candidate
   ulonglong2* acc;
   uint32_t *log_live, *log_ncand;
+  uint32_t* clist;  // V: component of the candidate at log position p, at p % V
   uint32_t* gc;
 };
 
@@ -155,7 +156,11 @@ __device__ __forceinline__ void book_samples(const RecArgs& a, uint32_t r, uint3
     }
   }
   base = __shfl_sync(0xffffffffu, base, 0);
-  if (cand) a.log_ids[base + __popc(m_cand & ((1u << lane) - 1))] = e;
+  if (cand) {
+    const uint32_t p = base + __popc(m_cand & ((1u << lane) - 1));
+    a.log_ids[p] = e;
+    a.clist[p % a.V] = K;  // a round logs at most V candidates: no two share p % V
+  }
 }
 
 // Position of this lane's item in ctr[key]'s range: lanes of the warp with
@@ -192,12 +197,144 @@ __device__ __forceinline__ void warp_xor_row(ulonglong2 (&acc)[kWarpBuckets], co
 constexpr uint32_t kBigFlag = 0x80000000u;  // roff[K] flag: K's members are in permb
 constexpr uint32_t kTileSegs = 2 + kRecTile / (kRecSpan + 1);  // components meeting one tile
 
+// Most candidates of a round whose hook runs in one CTA (shared memory)
+// instead of across the grid.
+constexpr uint32_t kSmallHook = 1024;
+
+// Root in a shared-memory forest with path halving; concurrent halving only
+// ever points a node at an ancestor.
+__device__ __forceinline__ uint32_t s_find(volatile uint32_t* par, uint32_t x) {
+  for (uint32_t k = 0; k < 2 * kSmallHook; k++) {  // a path is shorter than the node count
+    const uint32_t y = par[x];
+    if (y == x) break;
+    const uint32_t z = par[y];
+    if (z != y) par[x] = z;
+    x = y;
+  }
+  return x;
+}
+
+// The hook of a round with n <= kSmallHook candidates, run by one CTA: the
+// same minimum spanning forest by Boruvka as the grid-wide hook (a root's
+// key is edge << 11 | the root on the other side; two roots that chose the
+// same edge hook once, the larger under the smaller), over local node ids
+// (candidate i's component is node i; an endpoint component without a
+// candidate gets a node >= n), with __syncthreads between steps. Publishes
+// parent[] of the components that hooked and appends the forest edges.
+// smem: 36 KB.
+__device__ void small_hook(const RecArgs& a, uint32_t n, uint32_t lbase, unsigned char* smem) {
+  constexpr uint32_t kPer = kSmallHook / kRecThreads;  // candidates per thread
+  constexpr uint32_t kNodeBits = 11;                    // nodes < 2 * kSmallHook
+  static_assert(2 * kSmallHook <= (1u << kNodeBits), "node ids fit the key");
+  uint64_t* s_best = reinterpret_cast<uint64_t*>(smem);  // 2 * kSmallHook
+  uint32_t* s_par = reinterpret_cast<uint32_t*>(s_best + 2 * kSmallHook);
+  uint32_t* s_lab = s_par + 2 * kSmallHook;  // node -> component label
+  __shared__ uint32_t s_nn, s_nf, s_f0;
+  const uint32_t tid = threadIdx.x, bd = blockDim.x, V = a.V;
+  if (tid == 0) {
+    s_nn = n;
+    s_nf = 0;
+    s_f0 = ld_cg(&a.gc[GC_NFOREST]);  // the other CTAs wait at the grid barrier: this CTA owns the count
+  }
+  for (uint32_t x = tid; x < 2 * kSmallHook; x += bd) s_lab[x] = kNoneU32;
+  __syncthreads();
+  for (uint32_t i = tid; i < n; i += bd) {
+    const uint32_t K = ld_cg(&a.clist[(lbase + i) % V]);
+    s_lab[i] = K;
+    a.roff[K] = i;  // roff is free between the reduce and the next round
+  }
+  __syncthreads();
+  uint64_t ce[kPer];  // this thread's candidates: edge, node pair
+  uint32_t cab[kPer];
+#pragma unroll
+  for (uint32_t k = 0; k < kPer; k++) {
+    const uint32_t i = tid + k * bd;
+    cab[k] = kNoneU32;
+    ce[k] = 0;
+    if (i < n) {
+      const uint32_t K = s_lab[i];
+      const uint64_t lab = __ldcg(&a.cand[K]).y;
+      const uint32_t lu = (uint32_t)(lab >> 32), lv = (uint32_t)lab;
+      const uint32_t L = lu == K ? lv : lu;
+      uint32_t j = ld_cg(&a.roff[L]);
+      if (!(j < n && s_lab[j] == L)) {  // L has no candidate: one new node, first claim wins
+        const uint32_t mine = atomicAdd(&s_nn, 1u);
+        const uint32_t prev = atomicCAS(&a.pcount[L], 0u, mine + 1);
+        if (prev == 0) s_lab[mine] = L;
+        j = prev == 0 ? mine : prev - 1;
+      }
+      cab[k] = i | (j << 16);
+      ce[k] = ld_cg(&a.log_ids[lbase + i]);
+    }
+  }
+  __syncthreads();
+  const uint32_t nn = s_nn;
+  for (uint32_t x = tid; x < nn; x += bd) {
+    s_par[x] = x;
+    s_best[x] = kNone;
+  }
+  __syncthreads();
+  for (uint32_t iter = 0; iter < 64; iter++) {
+    int any = 0;
+#pragma unroll
+    for (uint32_t k = 0; k < kPer; k++) {
+      if (cab[k] == kNoneU32) continue;
+      const uint32_t ra = s_find(s_par, cab[k] & 0xFFFFu), rb = s_find(s_par, cab[k] >> 16);
+      if (ra != rb) {  // read first: most proposals to a big tree's root lose
+        const uint64_t ka = ce[k] << kNodeBits | rb, kb = ce[k] << kNodeBits | ra;
+        if (ka < s_best[ra]) atomicMin((unsigned long long*)&s_best[ra], (unsigned long long)ka);
+        if (kb < s_best[rb]) atomicMin((unsigned long long*)&s_best[rb], (unsigned long long)kb);
+        any = 1;
+      } else {
+        cab[k] = kNoneU32;  // both ends in one tree: never crosses again
+      }
+    }
+    if (!__syncthreads_or(any)) break;
+    for (uint32_t x = tid; x < nn; x += bd) {
+      const uint64_t key = s_best[x];
+      if (key == kNone) continue;
+      const uint64_t e = key >> kNodeBits;
+      const uint32_t o = (uint32_t)key & ((1u << kNodeBits) - 1);
+      if ((s_best[o] >> kNodeBits) != e || x > o) {
+        s_par[x] = o;
+        a.forest[s_f0 + atomicAdd(&s_nf, 1u)] = e;
+      }
+    }
+    __syncthreads();
+    // flatten by pointer jumping, so that the next finds take one hop (the
+    // hooks just made can form long chains); every value read is an ancestor
+    for (uint32_t x = tid; x < nn; x += bd) s_best[x] = kNone;
+    for (uint32_t pass = 0; pass < 16; pass++) {  // depth < 2^11 needs at most 11 passes
+      int moved = 0;
+      for (uint32_t x = tid; x < nn; x += bd) {
+        const uint32_t p = s_par[x], pp = s_par[p];
+        if (p != pp) {
+          s_par[x] = pp;
+          moved = 1;
+        }
+      }
+      if (!__syncthreads_or(moved)) break;
+    }
+  }
+  for (uint32_t x = tid; x < nn; x += bd) {
+    const uint32_t lab = s_lab[x];
+    if (lab == kNoneU32) continue;  // an id whose claim lost
+    const uint32_t rt = s_find(s_par, x);
+    if (rt != x) a.parent[lab] = s_lab[rt];
+    if (x >= n) a.pcount[lab] = 0;
+  }
+  if (tid == 0) a.gc[GC_NFOREST] = s_f0 + s_nf;
+}
+
 __global__ void __launch_bounds__(kRecThreads, 2) k_recover(RecArgs a) {
   __shared__ int s_ok;
   __shared__ uint32_t t_w[kRecTile], t_k[kRecTile];
   static_assert(kRecTile <= kRecThreads, "one member id per thread");
+  static_assert(sizeof(ulonglong2) * kTileSegs * kRecThreads >= 2 * kSmallHook * (8 + 4 + 4),
+                "small_hook lives in t_stage");
+  static_assert(kSmallHook % kRecThreads == 0, "small_hook: whole candidates per thread");
   __shared__ ulonglong2 t_stage[kTileSegs][kRecThreads];
-  __shared__ uint32_t t_seg_k[kTileSegs], t_seg_b[kTileSegs], t_seg_e[kTileSegs];
+  __shared__ uint32_t t_seg_k[kTileSegs];
   const uint32_t V = a.V, W = a.W, nb = gridDim.x, tid = threadIdx.x, lane = tid & 31;
   const uint32_t gtid = blockIdx.x * blockDim.x + tid, gstride = gridDim.x * blockDim.x;
   const uint32_t wpb = blockDim.x >> 5, gwarp = blockIdx.x * wpb + (tid >> 5), nwarps = gridDim.x * wpb;
@@ -310,7 +447,7 @@ __global__ void __launch_bounds__(kRecThreads, 2) k_recover(RecArgs a) {
         }
         __syncthreads();
         ulonglong2 acc1 = make_ulonglong2(0, 0);
-        uint32_t nseg = 0, segb = 0;
+        uint32_t nseg = 0;
         for (uint32_t m = 0; m < cnt; m += 8) {
           ulonglong2 x[8];
 #pragma unroll
@@ -327,13 +464,8 @@ __global__ void __launch_bounds__(kRecThreads, 2) k_recover(RecArgs a) {
               if (mm + 1 == cnt || t_k[mm + 1] != t_k[mm]) {  // a component's part ends here
                 t_stage[nseg][tid] = acc1;
                 acc1 = make_ulonglong2(0, 0);
-                if (tid == 0) {
-                  t_seg_k[nseg] = t_k[mm];
-                  t_seg_b[nseg] = segb;
-                  t_seg_e[nseg] = mm + 1;
-                }
+                if (tid == 0) t_seg_k[nseg] = t_k[mm];
                 nseg++;
-                segb = mm + 1;
               }
             }
           }
@@ -392,6 +524,8 @@ __global__ void __launch_bounds__(kRecThreads, 2) k_recover(RecArgs a) {
     uint64_t st_e = 0;
     for (uint32_t sp = gwarp; sp < nspans; sp += nwarps) {
       const uint32_t i0 = sp * span, cnt = min(span, nmem - i0);
+      if (r == 0 && sp + nwarps < nspans && lane * 8 < W)  // round 0: bring this warp's next row to L2
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(a.sketch + (size_t)(sp + nwarps) * W + lane * 8));
       uint32_t mw = 0, mk = kNoneU32;
       if (lane < cnt) {
         mw = r > 0 ? ld_cg(&a.perm[i0 + lane]) : i0 + lane;
@@ -469,37 +603,63 @@ __global__ void __launch_bounds__(kRecThreads, 2) k_recover(RecArgs a) {
     }
 
     // ---- hook: minimum spanning forest of the candidates by Boruvka. A
-    // root's key is edge*V + (root on the other side), so the min key names
+    // root's key is edge << vbits | (root on the other side), so the min key names
     // the min-id crossing edge and where it leads; two roots that chose the
-    // same edge hook once (the larger id under the smaller).
-    for (uint32_t iter = 0; iter < 64; iter++) {
+    // same edge hook once (the larger id under the smaller). A round with
+    // few candidates hooks in one CTA (small_hook) behind a single barrier.
+    const uint32_t ncand = ld_cg(&a.log_ncand[r]);
+    const uint32_t vbits = 32 - __clz(V - 1);  // bits of a vertex id (V <= 2^21: keys fit 64 bits)
+    const uint64_t vmask = (1ull << vbits) - 1;
+    if (ncand <= kSmallHook) {
+      if (blockIdx.x == 0)
+        small_hook(a, ncand, ld_cg(&gc[GC_LOGLEN]) - ncand, reinterpret_cast<unsigned char*>(&t_stage[0][0]));
+      CUPC_GRID_SYNC();
+    }
+    for (uint32_t iter = 0; ncand > kSmallHook && iter < 64; iter++) {
       uint64_t* bc = (iter & 1) ? a.best1 : a.best0;
       uint64_t* bn = (iter & 1) ? a.best0 : a.best1;
       const uint32_t act = (iter & 1) ? GC_ACTIVE_ODD : GC_ACTIVE, act_next = (iter & 1) ? GC_ACTIVE : GC_ACTIVE_ODD;
+      bool any = false;
       for (uint32_t K = gtid; K < V; K += gstride) {
         const ulonglong2 c = __ldcg(&a.cand[K]);
         if (c.x == kNone) continue;
         const uint64_t e = c.x;
         const uint32_t ra = find_root(a.parent, (uint32_t)(c.y >> 32), V);
         const uint32_t rb = find_root(a.parent, (uint32_t)c.y, V);
-        if (ra != rb) {
-          atomicMin((unsigned long long*)&bc[ra], (unsigned long long)(e * V + rb));
-          atomicMin((unsigned long long*)&bc[rb], (unsigned long long)(e * V + ra));
-          *(volatile uint32_t*)&gc[act] = 1u;
+        if (ra != rb) {  // read first: most proposals to a big tree's root lose
+          const uint64_t ka = e << vbits | rb, kb = e << vbits | ra;
+          if (ka < ld_cg(&bc[ra])) atomicMin((unsigned long long*)&bc[ra], (unsigned long long)ka);
+          if (kb < ld_cg(&bc[rb])) atomicMin((unsigned long long*)&bc[rb], (unsigned long long)kb);
+          any = true;
         }
       }
+      if (__any_sync(0xffffffffu, any) && lane == 0) *(volatile uint32_t*)&gc[act] = 1u;
       CUPC_GRID_SYNC();
       if (ld_cg(&gc[act]) == 0) break;
-      for (uint32_t x = gtid; x < V; x += gstride) {
-        bn[x] = kNone;
-        const uint64_t key = ld_cg(&bc[x]);
-        if (key == kNone) continue;
-        const uint64_t e = key / V;
-        const uint32_t o = (uint32_t)(key % V);
-        const bool mutual = ld_cg(&bc[o]) / V == e;
-        if (!mutual || x > o) {
-          a.parent[x] = o;
-          a.forest[atomicAdd(&gc[GC_NFOREST], 1u)] = e;
+      for (uint32_t base = gwarp * 32; base < V; base += nwarps * 32) {
+        const uint32_t x = base + lane;
+        bool hook = false;
+        uint64_t e = 0;
+        uint32_t o = 0;
+        if (x < V) {
+          bn[x] = kNone;
+          const uint64_t key = ld_cg(&bc[x]);
+          if (key != kNone) {
+            e = key >> vbits;
+            o = (uint32_t)(key & vmask);
+            const bool mutual = (ld_cg(&bc[o]) >> vbits) == e;
+            hook = !mutual || x > o;
+          }
+        }
+        const uint32_t m = __ballot_sync(0xffffffffu, hook);
+        if (m) {
+          uint32_t at = 0;
+          if (lane == 0) at = atomicAdd(&gc[GC_NFOREST], (uint32_t)__popc(m));
+          at = __shfl_sync(0xffffffffu, at, 0);
+          if (hook) {
+            a.parent[x] = o;
+            a.forest[at + __popc(m & ((1u << lane) - 1))] = e;
+          }
         }
       }
       if (gtid == 0) gc[act_next] = 0;
@@ -508,15 +668,30 @@ __global__ void __launch_bounds__(kRecThreads, 2) k_recover(RecArgs a) {
 
     // ---- relabel to the minimum vertex id of each component; clear the
     // round's scratch
-    for (uint32_t w = gtid; w < V; w += gstride) {
-      a.rcnt[w] = 0;
-      a.cand[w] = make_ulonglong2(kNone, 0);
-      a.best0[w] = kNone;
-      a.best1[w] = kNone;
-      if (ld_cg(&a.label[w]) != w) continue;
-      const uint32_t root = find_root(a.parent, w, V);
-      atomicMin(&a.minv[root], w);
-      if (root != w) a.merged[root] = 1;
+    for (uint32_t base = gwarp * 32; base < V; base += nwarps * 32) {
+      const uint32_t w = base + lane;
+      bool lab = false;
+      uint32_t root = 0;
+      if (w < V) {
+        a.rcnt[w] = 0;
+        a.cand[w] = make_ulonglong2(kNone, 0);
+        a.best0[w] = kNone;
+        a.best1[w] = kNone;
+        if (ld_cg(&a.label[w]) == w) {
+          lab = true;
+          root = find_root(a.parent, w, V);
+        }
+      }
+      const uint32_t act = __ballot_sync(0xffffffffu, lab);
+      if (lab) {  // the lanes of one root: min id and "merged" with one write each
+        const uint32_t peers = __match_any_sync(act, root);
+        const uint32_t mn = __reduce_min_sync(peers, w);
+        const bool mg = __any_sync(peers, root != w);
+        if (lane == (uint32_t)__ffs(peers) - 1) {
+          atomicMin(&a.minv[root], mn);
+          if (mg) a.merged[root] = 1;
+        }
+      }
     }
     if (gtid == 0) {
       gc[GC_NZ] = 0;
@@ -600,6 +775,7 @@ cudaError_t launch_recover(cupc_graph* g, cudaStream_t s) {
   a.acc = g->acc;
   a.log_live = g->log_live;
   a.log_ncand = g->log_ncand;
+  a.clist = g->clist;
   a.gc = g->gc;
   cudaError_t e = cudaMemsetAsync(g->gc + GC_BAR_COUNT, 0, sizeof(uint32_t), s);
   if (e != cudaSuccess) return e;

@@ -4,8 +4,9 @@
 //
 // One chunk of <= max_batch edges goes through four stream-ordered kernels:
 //   k_count   per-vertex record counts (2 records per edge, one per endpoint)
-//   k_plan    exclusive scan -> per-vertex cursors + work items of at most
-//             kItemRecords records of one vertex (single CTA)
+//   k_plan_count / k_plan_write
+//             exclusive scan over vertex slices -> per-vertex cursors and
+//             work items of at most item_records records of one vertex
 //   k_scatter endpoint records (the edge index u*V+v) grouped by vertex
 //   k_apply   persistent CTAs pull work items; thread (layer r, slot s)
 //             hashes every record of the item for column s of layer r (slot
@@ -58,23 +59,104 @@ __global__ void k_count(const uint32_t* __restrict__ edges, size_t n, uint32_t* 
   }
 }
 
-// Cursors and work items of one chunk (plan_vertices), single CTA. Resets
-// cnt for the next chunk.
-__global__ void __launch_bounds__(1024) k_plan(uint32_t* cnt, uint32_t* cursor, uint4* items, uint32_t V,
-                                                 uint32_t item_records, uint32_t* gc) {
+// Work plan of one chunk over many CTAs, in two launches that never wait on
+// one another. The vertices are cut into slices of 256 * vpt; slice b is
+// planned by CTA b. Kinds of vertices and the layout of records and items
+// are those of plan_vertices: direct-path vertices (<= kDirectMax records)
+// first in rec, then fold vertices, whose records are cut into items of
+// item_records; direct items of kDirectItemRecords follow the fold items.
+//
+// k_plan_count: per-slice totals {fold records, direct records, fold items}.
+__global__ void __launch_bounds__(256) k_plan_count(const uint32_t* __restrict__ cnt, uint32_t V, uint32_t vpt,
+                                                    uint32_t item_records, uint4* part, const uint32_t* gc) {
+  __shared__ uint32_t sw[3][32];
   if (ld_cg(&gc[GC_ERR]) & kErrInval) return;
-  uint32_t nd = 0;
-  const uint32_t nitems = plan_vertices(cnt, cursor, items, V, item_records, &nd);
-  if (threadIdx.x == 0) {
-    gc[GC_NITEMS] = nitems;
+  const uint32_t lo = blockIdx.x * blockDim.x * vpt, hi = min(V, lo + blockDim.x * vpt);
+  uint32_t v[3] = {0, 0, 0};
+  for (uint32_t w = lo + threadIdx.x; w < hi; w += blockDim.x) {
+    const uint32_t c = cnt[w];
+    if (c > kDirectMax) {
+      v[0] += c;
+      v[2] += (c + item_records - 1) / item_records;
+    } else {
+      v[1] += c;
+    }
+  }
+  uint32_t e[3], t[3];
+  block_scan3(v, e, t, sw);
+  if (threadIdx.x == 0) part[blockIdx.x] = make_uint4(t[0], t[1], t[2], 0u);
+}
+
+// k_plan_write: CTA b adds up the totals of slices < b (its offsets) and of
+// all slices (direct records nd, fold items), then scans its slice 256
+// vertices at a time, writing cursors and fold items; every CTA writes a
+// share of the direct items. Resets cnt for the next chunk.
+__global__ void __launch_bounds__(256) k_plan_write(uint32_t* cnt, uint32_t* cursor, uint4* items, uint32_t V,
+                                                    uint32_t vpt, uint32_t item_records, const uint4* __restrict__ part,
+                                                    uint32_t* gc) {
+  __shared__ uint32_t sw[3][32];
+  if (ld_cg(&gc[GC_ERR]) & kErrInval) return;
+  const uint32_t nb = gridDim.x, b = blockIdx.x;
+  // offsets of this slice and the grand totals
+  uint32_t before[3] = {0, 0, 0}, all[3] = {0, 0, 0};
+  for (uint32_t j = threadIdx.x; j < nb; j += blockDim.x) {
+    const uint4 p = part[j];
+    all[0] += p.x;
+    all[1] += p.y;
+    all[2] += p.z;
+    if (j < b) {
+      before[0] += p.x;
+      before[1] += p.y;
+      before[2] += p.z;
+    }
+  }
+  uint32_t e[3], tb[3], ta[3];
+  block_scan3(before, e, tb, sw);
+  block_scan3(all, e, ta, sw);
+  const uint32_t nd = ta[1], nfold = ta[2];
+  uint32_t carry[3] = {nd + tb[0], tb[1], tb[2]};  // next fold record, direct record, fold item
+  const uint32_t lo = b * blockDim.x * vpt, hi = min(V, lo + blockDim.x * vpt);
+  for (uint32_t base = lo; base < hi; base += blockDim.x) {
+    const uint32_t w = base + threadIdx.x;
+    const uint32_t c = w < hi ? cnt[w] : 0;
+    const bool fold = c > kDirectMax;
+    const uint32_t ni = fold ? (c + item_records - 1) / item_records : 0;
+    const uint32_t v[3] = {fold ? c : 0, fold ? 0 : c, ni};
+    uint32_t t[3];
+    block_scan3(v, e, t, sw);
+    if (w < hi) {
+      cnt[w] = 0;
+      if (fold) {
+        const uint32_t pf = carry[0] + e[0], pi = carry[2] + e[2];
+        cursor[w] = pf;
+        for (uint32_t q = 0; q < ni; q++) {
+          const uint32_t bg = pf + q * item_records;
+          items[pi + q] = make_uint4(w, bg, min(pf + c, bg + item_records), ni == 1 ? 1u : 0u);
+        }
+      } else {
+        cursor[w] = carry[1] + e[1];
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 3; k++) carry[k] += t[k];
+  }
+  const uint32_t ndi = (nd + kDirectItemRecords - 1) / kDirectItemRecords;
+  for (uint32_t q = b * blockDim.x + threadIdx.x; q < ndi; q += nb * blockDim.x)
+    items[nfold + q] = make_uint4(kDirectItem, q * kDirectItemRecords, min(nd, (q + 1) * kDirectItemRecords), 0u);
+  if (b == 0 && threadIdx.x == 0) {
+    gc[GC_NITEMS] = nfold + ndi;
     gc[GC_NDIRECT] = nd;
     gc[GC_NEXT_ITEM] = 0;
     gc[GC_BATCHES] += 1;
   }
 }
 
-// Endpoint records grouped by vertex; records of direct-path vertices (the
-// first nd positions) also note their vertex.
+// Slice width of the plan kernels: at most kPlanSlices slices.
+uint32_t plan_vpt(uint32_t V) {
+  const uint32_t per = 256u * kPlanSlices;
+  return std::max(1u, (V + per - 1) / per);
+}
+
 __global__ void k_scatter(const uint32_t* __restrict__ edges, size_t n, uint32_t V, uint32_t* cursor,
                           uint64_t* __restrict__ rec, uint32_t* __restrict__ recw, const uint32_t* gc) {
   if (ld_cg(&gc[GC_ERR]) & kErrInval) return;
@@ -171,9 +253,11 @@ cudaError_t launch_update_chunk(cupc_graph* g, const uint32_t* edges, size_t n, 
   if (n == 0) return cudaSuccess;
   int grid = (int)std::min<size_t>((n + 255) / 256, (size_t)g->sms * 8);
   {
-    ProfScope ps(g, s, PC_GROUP, 3);
+    ProfScope ps(g, s, PC_GROUP, 4);
     k_count<<<grid, 256, 0, s>>>(edges, n, g->cnt, g->gc);
-    k_plan<<<1, 1024, 0, s>>>(g->cnt, g->cursor, g->items, g->V, g->item_records, g->gc);
+    const uint32_t vpt = plan_vpt(g->V), nb = (g->V + 256 * vpt - 1) / (256 * vpt);
+    k_plan_count<<<nb, 256, 0, s>>>(g->cnt, g->V, vpt, g->item_records, g->part, g->gc);
+    k_plan_write<<<nb, 256, 0, s>>>(g->cnt, g->cursor, g->items, g->V, vpt, g->item_records, g->part, g->gc);
     k_scatter<<<grid, 256, 0, s>>>(edges, n, g->V, g->cursor, g->rec, g->recw, g->gc);
   }
   ProfScope ps(g, s, PC_APPLY, 1);

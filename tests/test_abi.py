@@ -54,6 +54,10 @@ def test_workspace_bytes(C):
     assert C.cupc_workspace_bytes(1000, (0, 0, 64, 0)) == 0  # D > 63
     assert C.cupc_workspace_bytes(1000, (0, 31, 30, 0)) == 0  # W > 256
     assert C.cupc_workspace_bytes(1000, (3, 2, 5, 100)) > 0
+    assert C.cupc_workspace_bytes(1000, (64, 16, 2, 0)) == 0  # 64 layers x 32 lanes > 1024 threads
+    assert C.cupc_workspace_bytes(1000, (32, 16, 2, 0)) > 0
+    assert C.cupc_workspace_bytes(1 << 21, (0, 0, 8, 1 << 10)) > 0
+    assert C.cupc_workspace_bytes((1 << 21) + 1, (0, 0, 8, 1 << 10)) == 0  # edge and vertex id share a key
     assert C.cupc_workspace_bytes(1000, (0, 0, 0, 1 << 20)) > C.cupc_workspace_bytes(1000, (0, 0, 0, 1 << 10))
 
 

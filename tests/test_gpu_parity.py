@@ -66,6 +66,19 @@ def test_sketches_and_recovery_bit_exact(V, p, seed):
     assert dev.sync() == (0 if ref.stats()["complete"] else 3)
 
 
+@pytest.mark.parametrize("V,p,seed", [(20000, 0.0001, 8), (40000, 0.00004, 9)])
+def test_recovery_with_many_candidates_after_round_0(V, p, seed):
+    # sparse graphs whose round 1 still has more than 1024 candidates: later
+    # rounds hook across the grid as well as in one CTA (up to 1024)
+    E = WL.er_edges(V, p, seed)
+    dev, ref = _dev(V, seed), O.Graph(V, seed)
+    assert dev.update(E) == 0
+    assert ref.update(E) == O.OK
+    assert_same_recovery(dev, ref)
+    ncand = [len(ids) for _, ids in ref.round_log()]
+    assert ncand[1] > 1024 and min(ncand[2:]) <= 1024
+
+
 def test_plain_stream_full_size():
     # V=1024: ER(0.5) start graph, 200k uniform toggles, 1k-pair Connected
     # batch every 10k updates; every answer and the final sketch bit-exact
