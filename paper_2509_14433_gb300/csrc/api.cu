@@ -55,7 +55,7 @@ Dims derive(uint32_t V, const cupc_params* p) {
 struct Layout {
   size_t sketch, keys, gc, cnt, cursor, rec, recw, items, part, stage_edges, stage_ops, label, parent, minv, rcnt, roff,
       perm, permb, pcount, final_, merged, best, best2, cand, forest, forest_sorted, acc, log_ids, log_live,
-      log_ncand, clist, total;
+      log_ncand, hlist, total;
 };
 
 Layout layout(const Dims& d) {
@@ -98,7 +98,7 @@ Layout layout(const Dims& d) {
   l.log_ids = take((size_t)d.L * V * 8);
   l.log_live = take(d.L * 4);
   l.log_ncand = take(d.L * 4);
-  l.clist = take(V * 4);
+  l.hlist = take(kSmallHook * sizeof(ulonglong2));
   l.total = off;
   return l;
 }
@@ -213,7 +213,7 @@ cupc_status cupc_init(uint32_t V, uint64_t seed, const cupc_params* params, void
   g->log_ids = (uint64_t*)(b + l.log_ids);
   g->log_live = (uint32_t*)(b + l.log_live);
   g->log_ncand = (uint32_t*)(b + l.log_ncand);
-  g->clist = (uint32_t*)(b + l.clist);
+  g->hlist = (ulonglong2*)(b + l.hlist);
   if (setup_update(g) != cudaSuccess || setup_recover(g) != cudaSuccess) {
     cudaGetLastError();
     return fail(CUPC_ECUDA);

@@ -46,6 +46,9 @@ constexpr uint32_t kRecSpan = 8;  // also the largest "small" component
 // Members per CTA tile when reducing big components.
 constexpr uint32_t kRecTile = 64;
 constexpr uint32_t kWarpBuckets = 8;  // buckets per lane in the recovery: W <= 256
+// Crossing candidates at or below which a recovery hook finishes in one CTA
+// (shared memory) instead of across the grid.
+constexpr uint32_t kSmallHook = 1024;
 // Bounded device-side waits give up after this long.
 constexpr uint64_t kWaitLimitNs = 2000000000ull;
 
@@ -56,14 +59,14 @@ enum : uint32_t {
   GC_NEXT_ITEM = 2,  // dynamic scheduler cursor of the apply kernel
   GC_NFOREST = 3,
   GC_NZ = 4,         // non-ZERO samples this round
-  GC_ACTIVE = 5,     // MSF: candidates still crossing components (even iterations)
+  GC_ACTIVE = 5,     // MSF: candidates still crossing two trees (even hook steps)
   GC_NMEMBERS = 6,   // live members this round
   GC_NFAIL = 7,
   GC_NFP = 8,
   GC_ROUNDS = 9,
   GC_COMPLETE = 10,
   GC_LOGLEN = 11,
-  GC_ACTIVE_ODD = 12,  // MSF: same flag for odd iterations
+  GC_ACTIVE_ODD = 12,  // MSF: same count for odd hook steps
   GC_BAR_COUNT = 13,
   GC_RECOVERIES = 15,
   GC_BATCHES = 16,   // update chunks applied
@@ -150,7 +153,7 @@ struct cupc_graph {
   uint64_t* log_ids; // L*V
   uint32_t* log_live;   // L
   uint32_t* log_ncand;  // L
-  uint32_t* clist;      // V: component of each logged candidate of a round
+  ulonglong2* hlist;    // kSmallHook: crossing candidates of a hook step (recovery)
   cupc_status last_recovery;
   // profiling: (kernel class, start, stop, launches) per recorded launch group
   struct ProfRec {

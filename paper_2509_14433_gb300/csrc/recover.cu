@@ -35,7 +35,7 @@ struct RecArgs {
   ulonglong2* cand;  // {edge, label[u] << 32 | label[v]} of a component's candidate
   ulonglong2* acc;
   uint32_t *log_live, *log_ncand;
-  uint32_t* clist;  // V: component of the candidate at log position p, at p % V
+  ulonglong2* hlist;  // kSmallHook: crossing candidates {edge, root_a << 32 | root_b} of a hook step
   uint32_t* gc;
 };
 
@@ -156,11 +156,7 @@ __device__ __forceinline__ void book_samples(const RecArgs& a, uint32_t r, uint3
     }
   }
   base = __shfl_sync(0xffffffffu, base, 0);
-  if (cand) {
-    const uint32_t p = base + __popc(m_cand & ((1u << lane) - 1));
-    a.log_ids[p] = e;
-    a.clist[p % a.V] = K;  // a round logs at most V candidates: no two share p % V
-  }
+  if (cand) a.log_ids[base + __popc(m_cand & ((1u << lane) - 1))] = e;
 }
 
 // Position of this lane's item in ctr[key]'s range: lanes of the warp with
@@ -197,9 +193,6 @@ __device__ __forceinline__ void warp_xor_row(ulonglong2 (&acc)[kWarpBuckets], co
 constexpr uint32_t kBigFlag = 0x80000000u;  // roff[K] flag: K's members are in permb
 constexpr uint32_t kTileSegs = 2 + kRecTile / (kRecSpan + 1);  // components meeting one tile
 
-// Most candidates of a round whose hook runs in one CTA (shared memory)
-// instead of across the grid.
-constexpr uint32_t kSmallHook = 1024;
 
 // Root in a shared-memory forest with path halving; concurrent halving only
 // ever points a node at an ancestor.
@@ -214,58 +207,65 @@ __device__ __forceinline__ uint32_t s_find(volatile uint32_t* par, uint32_t x) {
   return x;
 }
 
-// The hook of a round with n <= kSmallHook candidates, run by one CTA: the
-// same minimum spanning forest by Boruvka as the grid-wide hook (a root's
-// key is edge << 11 | the root on the other side; two roots that chose the
-// same edge hook once, the larger under the smaller), over local node ids
-// (candidate i's component is node i; an endpoint component without a
-// candidate gets a node >= n), with __syncthreads between steps. Publishes
-// parent[] of the components that hooked and appends the forest edges.
-// smem: 36 KB.
-__device__ void small_hook(const RecArgs& a, uint32_t n, uint32_t lbase, unsigned char* smem) {
+// The rest of a hook, run by one CTA once at most kSmallHook candidates
+// still cross two trees (hlist[0..n): edge, both current roots): the same
+// minimum spanning forest by Boruvka as the grid-wide steps (a root's key is
+// edge << 11 | the root on the other side; two roots that chose the same
+// edge hook once, the larger under the smaller), over local node ids, with
+// __syncthreads between steps and pointer jumping after each hook step.
+// Publishes parent[] of the roots that hooked and appends the forest edges.
+// smem: 32 KB.
+__device__ void small_hook(const RecArgs& a, uint32_t n, unsigned char* smem) {
   constexpr uint32_t kPer = kSmallHook / kRecThreads;  // candidates per thread
   constexpr uint32_t kNodeBits = 11;                    // nodes < 2 * kSmallHook
   static_assert(2 * kSmallHook <= (1u << kNodeBits), "node ids fit the key");
   uint64_t* s_best = reinterpret_cast<uint64_t*>(smem);  // 2 * kSmallHook
   uint32_t* s_par = reinterpret_cast<uint32_t*>(s_best + 2 * kSmallHook);
-  uint32_t* s_lab = s_par + 2 * kSmallHook;  // node -> component label
+  uint32_t* s_lab = s_par + 2 * kSmallHook;  // node -> global root
   __shared__ uint32_t s_nn, s_nf, s_f0;
-  const uint32_t tid = threadIdx.x, bd = blockDim.x, V = a.V;
+  const uint32_t tid = threadIdx.x, bd = blockDim.x;
   if (tid == 0) {
-    s_nn = n;
+    s_nn = 0;
     s_nf = 0;
     s_f0 = ld_cg(&a.gc[GC_NFOREST]);  // the other CTAs wait at the grid barrier: this CTA owns the count
   }
   for (uint32_t x = tid; x < 2 * kSmallHook; x += bd) s_lab[x] = kNoneU32;
   __syncthreads();
-  for (uint32_t i = tid; i < n; i += bd) {
-    const uint32_t K = ld_cg(&a.clist[(lbase + i) % V]);
-    s_lab[i] = K;
-    a.roff[K] = i;  // roff is free between the reduce and the next round
-  }
-  __syncthreads();
+  // node ids of the roots: the first claim of root x (a CAS on pcount[x],
+  // zero at rest during the hook and cleared again at the end) takes a new
+  // id, later claims read it; an id whose claim lost stays unused. All of a
+  // thread's claims are in flight at once.
   uint64_t ce[kPer];  // this thread's candidates: edge, node pair
-  uint32_t cab[kPer];
+  uint32_t cab[kPer], root[2 * kPer], mine[2 * kPer], prev[2 * kPer];
 #pragma unroll
   for (uint32_t k = 0; k < kPer; k++) {
     const uint32_t i = tid + k * bd;
-    cab[k] = kNoneU32;
-    ce[k] = 0;
+    ce[k] = kNone;
     if (i < n) {
-      const uint32_t K = s_lab[i];
-      const uint64_t lab = __ldcg(&a.cand[K]).y;
-      const uint32_t lu = (uint32_t)(lab >> 32), lv = (uint32_t)lab;
-      const uint32_t L = lu == K ? lv : lu;
-      uint32_t j = ld_cg(&a.roff[L]);
-      if (!(j < n && s_lab[j] == L)) {  // L has no candidate: one new node, first claim wins
-        const uint32_t mine = atomicAdd(&s_nn, 1u);
-        const uint32_t prev = atomicCAS(&a.pcount[L], 0u, mine + 1);
-        if (prev == 0) s_lab[mine] = L;
-        j = prev == 0 ? mine : prev - 1;
-      }
-      cab[k] = i | (j << 16);
-      ce[k] = ld_cg(&a.log_ids[lbase + i]);
+      const ulonglong2 h = __ldcg(&a.hlist[i]);
+      ce[k] = h.x;
+      root[2 * k] = (uint32_t)(h.y >> 32);
+      root[2 * k + 1] = (uint32_t)h.y;
     }
+  }
+#pragma unroll
+  for (uint32_t j = 0; j < 2 * kPer; j++)
+    if (ce[j / 2] != kNone) mine[j] = atomicAdd(&s_nn, 1u);
+#pragma unroll
+  for (uint32_t j = 0; j < 2 * kPer; j++)
+    if (ce[j / 2] != kNone) prev[j] = atomicCAS(&a.pcount[root[j]], 0u, mine[j] + 1);
+#pragma unroll
+  for (uint32_t k = 0; k < kPer; k++) {
+    cab[k] = kNoneU32;
+    if (ce[k] == kNone) continue;
+    uint32_t node[2];
+#pragma unroll
+    for (uint32_t q = 0; q < 2; q++) {
+      const uint32_t j = 2 * k + q;
+      if (prev[j] == 0) s_lab[mine[j]] = root[j];
+      node[q] = prev[j] == 0 ? mine[j] : prev[j] - 1;
+    }
+    cab[k] = node[0] | (node[1] << 16);
   }
   __syncthreads();
   const uint32_t nn = s_nn;
@@ -321,7 +321,7 @@ __device__ void small_hook(const RecArgs& a, uint32_t n, uint32_t lbase, unsigne
     if (lab == kNoneU32) continue;  // an id whose claim lost
     const uint32_t rt = s_find(s_par, x);
     if (rt != x) a.parent[lab] = s_lab[rt];
-    if (x >= n) a.pcount[lab] = 0;
+    a.pcount[lab] = 0;
   }
   if (tid == 0) a.gc[GC_NFOREST] = s_f0 + s_nf;
 }
@@ -607,35 +607,48 @@ __global__ void __launch_bounds__(kRecThreads, 2) k_recover(RecArgs a) {
     // the min-id crossing edge and where it leads; two roots that chose the
     // same edge hook once (the larger id under the smaller). A round with
     // few candidates hooks in one CTA (small_hook) behind a single barrier.
-    const uint32_t ncand = ld_cg(&a.log_ncand[r]);
     const uint32_t vbits = 32 - __clz(V - 1);  // bits of a vertex id (V <= 2^21: keys fit 64 bits)
     const uint64_t vmask = (1ull << vbits) - 1;
-    if (ncand <= kSmallHook) {
-      if (blockIdx.x == 0)
-        small_hook(a, ncand, ld_cg(&gc[GC_LOGLEN]) - ncand, reinterpret_cast<unsigned char*>(&t_stage[0][0]));
-      CUPC_GRID_SYNC();
-    }
-    for (uint32_t iter = 0; ncand > kSmallHook && iter < 64; iter++) {
+    for (uint32_t iter = 0; iter < 64; iter++) {
       uint64_t* bc = (iter & 1) ? a.best1 : a.best0;
       uint64_t* bn = (iter & 1) ? a.best0 : a.best1;
+      // candidates still crossing two trees: count them, list the first kSmallHook
       const uint32_t act = (iter & 1) ? GC_ACTIVE_ODD : GC_ACTIVE, act_next = (iter & 1) ? GC_ACTIVE : GC_ACTIVE_ODD;
-      bool any = false;
-      for (uint32_t K = gtid; K < V; K += gstride) {
-        const ulonglong2 c = __ldcg(&a.cand[K]);
-        if (c.x == kNone) continue;
-        const uint64_t e = c.x;
-        const uint32_t ra = find_root(a.parent, (uint32_t)(c.y >> 32), V);
-        const uint32_t rb = find_root(a.parent, (uint32_t)c.y, V);
-        if (ra != rb) {  // read first: most proposals to a big tree's root lose
-          const uint64_t ka = e << vbits | rb, kb = e << vbits | ra;
-          if (ka < ld_cg(&bc[ra])) atomicMin((unsigned long long*)&bc[ra], (unsigned long long)ka);
-          if (kb < ld_cg(&bc[rb])) atomicMin((unsigned long long*)&bc[rb], (unsigned long long)kb);
-          any = true;
+      for (uint32_t base = gwarp * 32; base < V; base += nwarps * 32) {
+        const uint32_t K = base + lane;
+        bool cross = false;
+        uint64_t e = 0;
+        uint32_t ra = 0, rb = 0;
+        if (K < V) {
+          const ulonglong2 c = __ldcg(&a.cand[K]);
+          if (c.x != kNone) {
+            e = c.x;
+            ra = find_root(a.parent, (uint32_t)(c.y >> 32), V);
+            rb = find_root(a.parent, (uint32_t)c.y, V);
+            if (ra != rb) {  // read first: most proposals to a big tree's root lose
+              const uint64_t ka = e << vbits | rb, kb = e << vbits | ra;
+              if (ka < ld_cg(&bc[ra])) atomicMin((unsigned long long*)&bc[ra], (unsigned long long)ka);
+              if (kb < ld_cg(&bc[rb])) atomicMin((unsigned long long*)&bc[rb], (unsigned long long)kb);
+              cross = true;
+            }
+          }
+        }
+        const uint32_t m = __ballot_sync(0xffffffffu, cross);
+        if (m) {
+          uint32_t at = 0;
+          if (lane == 0) at = atomicAdd(&gc[act], (uint32_t)__popc(m));
+          at = __shfl_sync(0xffffffffu, at, 0) + __popc(m & ((1u << lane) - 1));
+          if (cross && at < kSmallHook) a.hlist[at] = make_ulonglong2(e, (uint64_t)ra << 32 | rb);
         }
       }
-      if (__any_sync(0xffffffffu, any) && lane == 0) *(volatile uint32_t*)&gc[act] = 1u;
       CUPC_GRID_SYNC();
-      if (ld_cg(&gc[act]) == 0) break;
+      const uint32_t nact = ld_cg(&gc[act]);
+      if (nact == 0) break;
+      if (nact <= kSmallHook) {  // finish in one CTA behind a single barrier
+        if (blockIdx.x == 0) small_hook(a, nact, reinterpret_cast<unsigned char*>(&t_stage[0][0]));
+        CUPC_GRID_SYNC();
+        break;
+      }
       for (uint32_t base = gwarp * 32; base < V; base += nwarps * 32) {
         const uint32_t x = base + lane;
         bool hook = false;
@@ -775,7 +788,7 @@ cudaError_t launch_recover(cupc_graph* g, cudaStream_t s) {
   a.acc = g->acc;
   a.log_live = g->log_live;
   a.log_ncand = g->log_ncand;
-  a.clist = g->clist;
+  a.hlist = g->hlist;
   a.gc = g->gc;
   cudaError_t e = cudaMemsetAsync(g->gc + GC_BAR_COUNT, 0, sizeof(uint32_t), s);
   if (e != cudaSuccess) return e;
