@@ -72,6 +72,7 @@ enum : uint32_t {
   GC_BATCHES = 16,   // update chunks applied
   GC_NBIG = 17,      // members of big components this round
   GC_NDIRECT = 18,   // direct-path records of the current chunk
+  GC_NLIVE = 19,     // live components of the next recovery round
   GC_SLOTS = 32
 };
 

@@ -376,6 +376,19 @@ __global__ void __launch_bounds__(kRecThreads, 2) k_recover(RecArgs a) {
 
   for (uint32_t r = 0; r < a.L; r++) {
     const uint64_t kchk = a.keys[r * (a.C + 1) + a.C];
+    // One live component left: every other component is final, and a final
+    // component's merged sketch is zero (its cut is empty); the XOR of all
+    // vertex sketches of a layer is zero (each edge enters both endpoints),
+    // so the live one's merged sketch is zero too and it samples ZERO. Log
+    // the round as sampled (one live component, no candidate) and stop.
+    if (r > 0 && ld_cg(&gc[GC_NLIVE]) == 1) {
+      if (gtid == 0) {
+        a.log_live[r] = 1;
+        gc[GC_ROUNDS] = r + 1;
+        gc[GC_COMPLETE] = 1;
+      }
+      break;
+    }
     // ---- group the live vertices of round r by component: the relabel of
     // round r-1 counted them; give each component a segment (warp-aggregated
     // atomics), then scatter
@@ -712,6 +725,7 @@ __global__ void __launch_bounds__(kRecThreads, 2) k_recover(RecArgs a) {
       gc[GC_NBIG] = 0;
       gc[GC_ACTIVE] = 0;
       gc[GC_ACTIVE_ODD] = 0;
+      gc[GC_NLIVE] = 0;
     }
     CUPC_GRID_SYNC();
     // new labels; the members of next round's live components are counted
@@ -729,7 +743,9 @@ __global__ void __launch_bounds__(kRecThreads, 2) k_recover(RecArgs a) {
         if (w == root && mg) a.final_[nl] = 0;
         live = mg || !ld_cg(&a.final_[root]);
       }
-      warp_grab(a.rcnt, nl, live);
+      // the member that took position 0 of its component counts the component
+      const uint32_t m_first = __ballot_sync(0xffffffffu, warp_grab(a.rcnt, nl, live) == 0 && live);
+      if (lane == 0 && m_first) atomicAdd(&gc[GC_NLIVE], (uint32_t)__popc(m_first));
     }
     CUPC_GRID_SYNC();
   }
