@@ -122,16 +122,18 @@ def final_edge_set(V: int, steps) -> np.ndarray:
 def rmat_pairs(n: int, levels: int, probs, gen, device):
     """n R-MAT pairs over 2^levels vertices (Chakrabarti, Zhan, Faloutsos,
     SDM 2004): at each level pick quadrant a/b/c/d, i.e. (row bit, column bit)
-    = (0,0)/(0,1)/(1,0)/(1,1). Returns int64 tensors (u, v)."""
+    = (0,0)/(0,1)/(1,0)/(1,1), from one uniform draw r: the row bit is
+    r >= a+b, the column bit is a <= r < a+b or r >= a+b+c. Returns int64
+    tensors (u, v)."""
     import torch
     a, b, c, _ = probs
+    r = torch.rand((levels, n), generator=gen, device=device)
     u = torch.zeros(n, dtype=torch.int64, device=device)
     v = torch.zeros(n, dtype=torch.int64, device=device)
-    for _ in range(levels):
-        r = torch.rand(n, generator=gen, device=device)
-        q = (r >= a).long() + (r >= a + b).long() + (r >= a + b + c).long()
-        u = u * 2 + (q >> 1)
-        v = v * 2 + (q & 1)
+    for lv in range(levels):
+        rl = r[lv]
+        u.mul_(2).add_(rl >= a + b)
+        v.mul_(2).add_(((rl >= a) & (rl < a + b)) | (rl >= a + b + c))
     return u, v
 
 
@@ -143,8 +145,9 @@ class RmatStream:
     (positions drawn uniformly from the append-only list of inserted edges and
     kept if the edge is still present), the rest inserts R-MAT edges
     (self-loops and edges already present or repeated in the batch are
-    redrawn, up to 64 times, then replaced by uniform absent pairs; the count
-    of those fallbacks is kept). Within a batch the deletes come first, so
+    redrawn, in up to 64 passes sized by the previous pass's acceptance,
+    then replaced by uniform absent pairs; the count of those fallbacks is
+    kept). Within a batch the deletes come first, so
     applying the batch in order keeps the stream valid. Presence is a V^2-bit
     bitmap (2 GiB at V = 2^17) on the same device."""
 
@@ -161,13 +164,16 @@ class RmatStream:
         self.pool = torch.zeros(1 << 20, dtype=torch.int64, device=self.device)  # inserted ids, append-only
         self.n_inserted = 0
         self.fallbacks = 0
+        self.accept = 1.0  # acceptance of the last insert draw (sizes the next one)
 
     def _bits(self, ids):
         return (self.bitmap[ids >> 6] >> (ids & 63)) & 1
 
     def _flip(self, ids, sign):
+        # distinct bits of absent (present) edges: adding (subtracting) each
+        # power of two sets (clears) exactly that bit, wrap-around included
         one = self.torch.ones_like(ids)
-        self.bitmap.index_put_((ids >> 6,), sign * (one << (ids & 63)), accumulate=True)
+        self.bitmap.index_add_(0, ids >> 6, sign * (one << (ids & 63)))
 
     def _unique_keep(self, ids):
         u, inv = self.torch.unique(ids, return_inverse=True)
@@ -182,14 +188,17 @@ class RmatStream:
         x = t.rand(1, generator=self.gen, device=self.device).item()
         return int(np.exp(np.log(self.lo) + x * (np.log(self.hi) - np.log(self.lo))))
 
-    def _take(self, cand, want_bit, need):
+    def _take(self, cand, want_bit, need, counted=False):
         """Up to `need` ids of `cand` whose presence bit is `want_bit`, first
         occurrences only, in draw order; their bits are flipped at once, so
-        later draws of the same batch see them as taken."""
+        later draws of the same batch see them as taken. With `counted`, also
+        the number of such ids before the cut to `need`."""
         cand = cand[self._bits(cand) == want_bit]
-        cand = cand[self._unique_keep(cand)][:need]
+        cand = cand[self._unique_keep(cand)]
+        m = cand.numel()
+        cand = cand[:need]
         self._flip(cand, 1 if want_bit == 0 else -1)
-        return cand
+        return (cand, m) if counted else cand
 
     def _deletes(self, k):
         t = self.torch
@@ -210,13 +219,18 @@ class RmatStream:
     def _inserts(self, k):
         t = self.torch
         parts, have = [], 0
+        accept = self.accept
         for _ in range(64):
             need = k - have
             if need <= 0:
                 break
-            u, v = rmat_pairs(need, self.levels, self.probs, self.gen, self.device)
+            # draw in proportion to the last pass's acceptance (at most 16x,
+            # at most 2^23 pairs: the uniforms of all levels are held at once)
+            draw = min(16 * need, 1 << 23, max(1024, int(1.1 * need / accept)))
+            u, v = rmat_pairs(draw, self.levels, self.probs, self.gen, self.device)
             ok = u != v
-            got = self._take(t.minimum(u, v)[ok] * self.V + t.maximum(u, v)[ok], 0, need)
+            got, m = self._take(t.minimum(u, v)[ok] * self.V + t.maximum(u, v)[ok], 0, need, counted=True)
+            accept = max(m / draw, 1.0 / 16)
             parts.append(got)
             have += got.numel()
         while have < k:  # uniform absent pairs
@@ -228,6 +242,7 @@ class RmatStream:
             parts.append(got)
             have += got.numel()
             self.fallbacks += got.numel()
+        self.accept = accept
         got = t.cat(parts) if parts else t.zeros(0, dtype=t.int64, device=self.device)
         need = self.n_inserted + got.numel()
         if need > self.pool.numel():

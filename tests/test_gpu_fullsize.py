@@ -118,7 +118,8 @@ def test_dense_v16384_full_size():
 def test_cliques_v131072_full_size():
     # 256 disjoint 512-cliques joined by 8 batches of 64k random bridges and
     # split again by 8 shuffled batches deleting them; a 1k-pair query batch
-    # after every batch, checked against the exact components
+    # (half inside one clique, half across two) after every batch, checked
+    # against the exact components
     from paper_2509_14433_gb300 import cupc as C
     V, k, s, seed = 131072, 256, 512, 7
     g_rng = WL.rng(seed)
@@ -158,7 +159,13 @@ def test_cliques_v131072_full_size():
                 if rx != ry:
                     parent[rx] = ry
             root = np.array([find(c) for c in range(k)])
-            pr = WL.uniform_pairs(V, 1000, g_rng, distinct=False)
+            # 500 pairs inside one clique, 500 pairs across two cliques
+            cs = g_rng.integers(0, k, 500)
+            same = np.stack([perm[cs * s + g_rng.integers(0, s, 500)], perm[cs * s + g_rng.integers(0, s, 500)]], 1)
+            c1 = g_rng.integers(0, k, 500)
+            c2 = (c1 + g_rng.integers(1, k, 500)) % k
+            diff = np.stack([perm[c1 * s + g_rng.integers(0, s, 500)], perm[c2 * s + g_rng.integers(0, s, 500)]], 1)
+            pr = np.ascontiguousarray(np.concatenate([same, diff])[g_rng.permutation(1000)], np.uint32)
             out = torch.zeros(1000, dtype=torch.uint8, device="cuda")
             C.check(C.cupc_query(g, torch.from_numpy(pr.reshape(-1)).cuda(), 1000, out, None))
             want = root[comp[pr[:, 0]]] == root[comp[pr[:, 1]]]
