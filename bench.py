@@ -88,17 +88,24 @@ def expected_touched_buckets(counts, L, C, D):
 
 
 def apply_source_digest():
-    """md5 over what defines k_apply: the shared device header, the common
-    header and the kernel's own text in update.cu."""
+    """md5 over the source k_apply compiles from: the shared device header
+    (update_dev.cuh), the kernel's own text in update.cu, and the device
+    functions and error/counter constants of common.cuh (its other
+    declarations serve other kernels and the host)."""
     import hashlib
     import re
     csrc = os.path.join(ROOT, "paper_2509_14433_gb300", "csrc")
     h = hashlib.md5()
-    for f in ("update_dev.cuh", "common.cuh"):
-        h.update(open(os.path.join(csrc, f), "rb").read())
+    h.update(open(os.path.join(csrc, "update_dev.cuh"), "rb").read())
     upd = open(os.path.join(csrc, "update.cu")).read()
     m = re.search(r"__global__ void k_apply\(.*?\n}\n", upd, re.S)
     h.update((m.group(0) if m else upd).encode())
+    com = open(os.path.join(csrc, "common.cuh")).read()
+    for m in re.finditer(r"^__(?:host__ __)?device__ .*?\n}\n|^__device__ [^\n]*}\n", com, re.S | re.M):
+        h.update(m.group(0).encode())
+    for m in re.finditer(r"^constexpr uint32_t k(?:ErrInval|DirectItem\w*|SmemRows\w*|\w*ItemRecords) = [^;]*;|^  GC_(?:ERR|NITEMS|NEXT_ITEM) = \d+",
+                         com, re.M):
+        h.update(m.group(0).encode())
     return h.hexdigest()
 
 
