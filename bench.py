@@ -228,6 +228,9 @@ def run_gpu(args):
     C.check(st, "cupc_init")
     from paper_2509_14433_gb300 import autotune as AT
     tuned = AT.apply(g, V_DENSE, BATCH)  # tuned apply setting for 2^20-edge batches, if the table has one
+    tun = np.zeros(4, np.uint32)
+    C.cupc_get_tuning(g, tun)
+    apply_setting = [int(x) for x in tun[:3]]
     prm = np.zeros(4, np.uint32)
     C.cupc_get_params(g, prm)
     L, Cc, Dd, W = (int(x) for x in prm)
@@ -336,9 +339,7 @@ def run_gpu(args):
         pass
     peak = float(peaks.get("hbm_gbs", 6800.0))
     achieved = apply_bytes_per_launch / (apply_ms * 1e-3) / 1e9
-    tun = np.zeros(4, np.uint32)
-    C.cupc_get_tuning(g, tun)
-    traffic = apply_traffic([int(x) for x in tun[:3]])
+    traffic = apply_traffic(apply_setting)
     gpu_launches = int(nl_prof.sum())
     shares = {name: round(float(ms_prof[k]) / max(1e-9, float(ms_prof.sum())), 4)
               for k, name in enumerate(["validate", "group", "apply", "recover", "query", "sort"])}
@@ -361,6 +362,7 @@ def run_gpu(args):
                              "frac": achieved / peak, "traffic": traffic,
                              "kernel": "k_apply", "algorithmic_bytes_per_launch": apply_bytes_per_launch,
                              "edges_per_launch": BATCH, "avg_launch_ms": apply_ms,
+                             "apply_setting": apply_setting,
                              "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst copy)" if peaks else "fallback"},
                 "kernel_time_share": shares,
                 "query_latency_us": {"dense_after_batch_p50": statistics.median(lat_dense),

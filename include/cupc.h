@@ -95,7 +95,15 @@ cupc_status cupc_reset(cupc_graph* g, cupc_stream stream);
  * valid (insert only absent edges, delete only present ones) as Problem 1
  * requires. The whole batch is validated on the device first; any u == v,
  * u or v >= V, or op not +-1 drops the whole batch (sticky CUPC_EINVAL at
- * the next cupc_sync). n == 0 is a no-op. Marks the recovery stale. */
+ * the next cupc_sync). n == 0 is a no-op. Marks the recovery stale.
+ * edges and ops may be device or host memory. When both are host memory
+ * and n <= max_batch, they are copied on an internal stream into one of two
+ * staging buffers in turn, so that the copy overlaps the kernels of the
+ * previous batch: the copy waits for its staging buffer, not for earlier
+ * work on `stream`. So no earlier work on `stream` may still be writing
+ * these host buffers, and they must stay unchanged until `stream` has
+ * passed this call (as for cudaMemcpyAsync from pinned memory). Other host
+ * inputs are copied on `stream`. */
 cupc_status cupc_update_batch(cupc_graph* g, const uint32_t* edges, const int8_t* ops, size_t n,
                               cupc_stream stream);
 

@@ -53,7 +53,8 @@ Dims derive(uint32_t V, const cupc_params* p) {
 
 // Byte offsets of every device array inside the workspace.
 struct Layout {
-  size_t sketch, keys, gc, cnt, cursor, rec, recw, items, part, stage_edges, stage_ops, label, parent, minv, rcnt, roff,
+  size_t sketch, keys, gc, cnt, cursor, rec, recw, items, part, stage_edges, stage_ops, stage_edges1, stage_ops1,
+      label, parent, minv, rcnt, roff,
       perm, permb, pcount, final_, merged, best, best2, cand, forest, forest_sorted, acc, log_ids, log_live,
       log_ncand, hlist, total;
 };
@@ -79,6 +80,8 @@ Layout layout(const Dims& d) {
   l.part = take(kPlanSlices * sizeof(uint4));
   l.stage_edges = take(2 * B * 4);
   l.stage_ops = take(B);
+  l.stage_edges1 = take(2 * B * 4);
+  l.stage_ops1 = take(B);
   l.label = take(V * 4);
   l.parent = take(V * 4);
   l.minv = take(V * 4);
@@ -192,6 +195,8 @@ cupc_status cupc_init(uint32_t V, uint64_t seed, const cupc_params* params, void
   g->part = (uint4*)(b + l.part);
   g->stage_edges = (uint32_t*)(b + l.stage_edges);
   g->stage_ops = (int8_t*)(b + l.stage_ops);
+  g->stage_edges1 = (uint32_t*)(b + l.stage_edges1);
+  g->stage_ops1 = (int8_t*)(b + l.stage_ops1);
   g->stage_pairs = g->stage_edges;
   g->stage_out = (uint8_t*)g->stage_ops;
   g->label = (uint32_t*)(b + l.label);
@@ -236,6 +241,24 @@ cupc_status cupc_reset(cupc_graph* g, cupc_stream stream) {
   return CUPC_OK;
 }
 
+// The copy stream and slot events of host-input staging, made on first use.
+cudaError_t ensure_copy_stream(cupc_graph* g) {
+  if (g->copy_stream) return cudaSuccess;
+  cudaError_t e = cudaStreamCreateWithFlags(&g->copy_stream, cudaStreamNonBlocking);
+  for (int k = 0; k < 2 && e == cudaSuccess; k++) {
+    e = cudaEventCreateWithFlags(&g->slot_ready[k], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->slot_free[k], cudaEventDisableTiming);
+  }
+  return e;
+}
+
+// After the last kernel on s that reads staging slot k: a later copy into
+// slot k on the copy stream waits for this point.
+cudaError_t mark_slot_free(cupc_graph* g, int k, cudaStream_t s) {
+  cudaError_t e = ensure_copy_stream(g);  // so that a first async copy sees this use
+  return e == cudaSuccess ? cudaEventRecord(g->slot_free[k], s) : e;
+}
+
 cupc_status cupc_update_batch(cupc_graph* g, const uint32_t* edges, const int8_t* ops, size_t n,
                               cupc_stream stream) {
   if (!g) return CUPC_EINVAL;
@@ -247,8 +270,26 @@ cupc_status cupc_update_batch(cupc_graph* g, const uint32_t* edges, const int8_t
   if (dev_e && dev_o) {
     CUPC_TRY(launch_validate(g, edges, ops, n, s));
     for (size_t i = 0; i < n; i += B) CUPC_TRY(launch_update_chunk(g, edges + 2 * i, (n - i < B ? n - i : B), s));
+  } else if (!dev_e && !dev_o && n <= B) {
+    // host input, one chunk: copy on the graph's copy stream into the
+    // staging slot not used last, so that the copy overlaps the kernels of
+    // the previous batch; the copy waits only for its slot to be free
+    CUPC_TRY(ensure_copy_stream(g));
+    const int k = g->next_slot;
+    g->next_slot ^= 1;
+    uint32_t* se = k ? g->stage_edges1 : g->stage_edges;
+    int8_t* so = k ? g->stage_ops1 : g->stage_ops;
+    CUPC_TRY(cudaStreamWaitEvent(g->copy_stream, g->slot_free[k], 0));
+    CUPC_TRY(cudaMemcpyAsync(se, edges, 2 * n * sizeof(uint32_t), cudaMemcpyHostToDevice, g->copy_stream));
+    CUPC_TRY(cudaMemcpyAsync(so, ops, n, cudaMemcpyHostToDevice, g->copy_stream));
+    CUPC_TRY(cudaEventRecord(g->slot_ready[k], g->copy_stream));
+    CUPC_TRY(cudaStreamWaitEvent(s, g->slot_ready[k], 0));
+    CUPC_TRY(launch_validate(g, se, so, n, s));
+    CUPC_TRY(launch_update_chunk(g, se, n, s));
+    CUPC_TRY(mark_slot_free(g, k, s));
   } else {
-    // host input: stage chunk by chunk; a multi-chunk batch is validated in
+    // a host input mixed with a device one, or several chunks: stage in
+    // slot 0 on the caller's stream; a multi-chunk batch is validated in
     // a first pass so that a bad entry drops the whole batch
     auto stage = [&](size_t i, size_t k) -> cudaError_t {
       cudaError_t e = cudaMemcpyAsync(g->stage_edges, edges + 2 * i, 2 * k * sizeof(uint32_t),
@@ -273,6 +314,7 @@ cupc_status cupc_update_batch(cupc_graph* g, const uint32_t* edges, const int8_t
         CUPC_TRY(launch_update_chunk(g, g->stage_edges, k, s));
       }
     }
+    CUPC_TRY(mark_slot_free(g, 0, s));
   }
   g->dirty = true;
   return CUPC_OK;
@@ -302,6 +344,7 @@ cupc_status cupc_query(cupc_graph* g, const uint32_t* pairs, size_t m, uint8_t* 
     CUPC_TRY(launch_query(g, p, k, o, s));
     if (!dev_out) CUPC_TRY(cudaMemcpyAsync(out + i, g->stage_out, k, cudaMemcpyDeviceToHost, s));
   }
+  CUPC_TRY(mark_slot_free(g, 0, s));  // the query staging is update slot 0
   if (!dev_out) CUPC_TRY(cudaStreamSynchronize(s));
   return CUPC_OK;
 }
@@ -484,6 +527,13 @@ cupc_status cupc_get_params(const cupc_graph* g, uint32_t* out4) {
 void cupc_destroy(cupc_graph* g) {
   if (!g) return;
   prof_drain(g);
+  if (g->copy_stream) {  // released once their pending work completes
+    for (int k = 0; k < 2; k++) {
+      cudaEventDestroy(g->slot_ready[k]);
+      cudaEventDestroy(g->slot_free[k]);
+    }
+    cudaStreamDestroy(g->copy_stream);
+  }
   if (g->owns_ws && g->ws) {
     cudaDeviceSynchronize();
     cudaFree(g->ws);

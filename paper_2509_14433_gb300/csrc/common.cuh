@@ -130,8 +130,16 @@ struct cupc_graph {
   uint32_t* recw;      // 2*max_batch: vertex of each direct-path record
   uint4* items;        // 4*max_batch/kMinItemRecords + min(V, 2*max_batch) + 1
   uint4* part;         // kPlanSlices per-slice totals of the plan
-  uint32_t* stage_edges;  // 2*max_batch
+  uint32_t* stage_edges;  // 2*max_batch (host-input staging slot 0)
   int8_t* stage_ops;      // max_batch
+  uint32_t* stage_edges1;  // 2*max_batch (slot 1)
+  int8_t* stage_ops1;      // max_batch
+  // host inputs of cupc_update_batch are copied on copy_stream into the two
+  // slots in turn: slot_ready[k] after a copy, slot_free[k] after the last
+  // kernel (on the caller's stream) that reads slot k
+  cudaStream_t copy_stream;
+  cudaEvent_t slot_ready[2], slot_free[2];
+  int next_slot;
   uint32_t* stage_pairs;  // 2*max_pairs
   uint8_t* stage_out;     // max_pairs
   // recovery state

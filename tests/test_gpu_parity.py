@@ -165,6 +165,40 @@ def test_chunked_batches_and_host_buffers(host):
     assert dev.stats()["chunks"] >= 7 if not host else True
 
 
+def test_host_batches_in_a_row_alternate_staging():
+    # host batches are copied on the graph's copy stream into two staging
+    # buffers in turn; pinned and pageable buffers, a host query (which
+    # stages on the caller's stream) and a mixed host/device batch between
+    from paper_2509_14433_gb300 import cupc as C
+    V = 3000
+    dev, ref = _dev(V, 21, (0, 0, 0, 5000)), O.Graph(V, 21)
+    g = WL.rng(21)
+    keep = []
+    for k in range(12):
+        E = WL.uniform_pairs(V, 4000, g)
+        if k % 2:
+            e = torch.from_numpy(E.reshape(-1).copy()).pin_memory()
+            o = torch.ones(len(E), dtype=torch.int8).pin_memory()
+        else:
+            e, o = E.reshape(-1).copy(), np.ones(len(E), np.int8)
+        keep.append((e, o))
+        assert C.cupc_update_batch(dev.h, e, o, len(E), None) == 0
+        ref.update(E)
+        if k == 5:
+            pairs = WL.uniform_pairs(V, 300, g, distinct=False)
+            s1, a1 = dev.query(pairs, host=True)
+            s2, a2 = ref.query(pairs)
+            assert s1 == 0 and np.array_equal(a1, a2)
+        if k == 8:
+            M = WL.uniform_pairs(V, 2000, g)
+            ed = torch.from_numpy(M.reshape(-1).copy()).cuda()
+            assert C.cupc_update_batch(dev.h, ed, np.ones(len(M), np.int8), len(M), None) == 0
+            ref.update(M)
+    torch.cuda.synchronize()
+    assert np.array_equal(dev.export(), ref.export())
+    assert_same_recovery(dev, ref)
+
+
 @pytest.mark.parametrize("host", [False, True])
 def test_invalid_batch_is_dropped_whole_and_sticky(host):
     V = 50
