@@ -314,6 +314,7 @@ def run_gpu(args):
         C.check(C.cupc_query(g, p_d, 1000, q_out, stream))
         torch.cuda.synchronize()
         lat_dense.append((time.perf_counter() - t) * 1e6)
+    sweep = batch_latency_sweep(torch, C, g, D_d, ins_d, del_d, p_d, q_out, stream)
     C.cupc_destroy(g)
     del E_d, D_d, ins_d, del_d
 
@@ -365,6 +366,7 @@ def run_gpu(args):
                              "apply_setting": apply_setting,
                              "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst copy)" if peaks else "fallback"},
                 "kernel_time_share": shares,
+                "batch_size_vs_query_latency": sweep,
                 "query_latency_us": {"dense_after_batch_p50": statistics.median(lat_dense),
                                      "dense_after_batch_p99": float(np.percentile(lat_dense, 99)),
                                      **plain},
@@ -608,6 +610,34 @@ def plain_stream_latency(torch, C, dev, stream):
     C.cupc_destroy(g)
     return {"plain_v1024_p50": statistics.median(lat), "plain_v1024_p99": float(np.percentile(lat, 99)),
             "plain_v1024_toggle_updates_per_s": n_upd / upd_t, "plain_v1024_queries": len(lat)}
+
+
+def batch_latency_sweep(torch, C, g, D_d, ins_d, del_d, p_d, q_out, stream):
+    """Update batch size against the latency of the next Connected query
+    batch (the trade-off the paper's update buffering makes): for each size
+    b, insert then delete the first b of the deleted edges (absent, then
+    present: a valid stream) and ask 1k pairs after each batch. Latency =
+    host submit of the batch to the query's answer, recovery included."""
+    out = {}
+    for b in (1 << 10, 1 << 14, 1 << 17, 1 << 20, 1 << 22):
+        upd, lat = [], []
+        for k in range(9):  # the first pass warms up
+            ops = ins_d if k % 2 == 0 else del_d
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            C.check(C.cupc_update_batch(g, D_d, ops, b, stream))
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            C.check(C.cupc_query(g, p_d, 1000, q_out, stream))
+            torch.cuda.synchronize()
+            t2 = time.perf_counter()
+            if k:
+                upd.append(t1 - t0)
+                lat.append((t2 - t0) * 1e6)
+        C.check(C.cupc_update_batch(g, D_d, del_d, b, stream))  # the last pass inserted: leave the graph as it was
+        out[str(b)] = {"updates_per_s": b / statistics.median(upd), "query_p50_us": statistics.median(lat),
+                       "query_p99_us": float(np.percentile(lat, 99))}
+    return out
 
 
 def run_apply_profile(args):

@@ -68,7 +68,7 @@ Layout layout(const Dims& d) {
     return at;
   };
   const size_t V = d.V, B = d.max_batch;
-  const size_t nitems = 4 * B / kMinItemRecords + (V < 2 * B ? V : 2 * B) + 1;
+  const size_t nitems = 4 * B / kMinItemRecords + (V < 2 * B ? V : 2 * B) + 2 * kPlanGridCap + 1;
   l.sketch = take((size_t)d.L * V * d.W * sizeof(ulonglong2));
   l.keys = take((size_t)d.L * (d.C + 1) * sizeof(uint64_t));
   l.gc = take(GC_SLOTS * sizeof(uint32_t));

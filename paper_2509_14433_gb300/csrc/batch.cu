@@ -168,17 +168,16 @@ __global__ void k_apply_m(BatchHead* __restrict__ h, uint32_t rmax, uint32_t ite
   __shared__ uint32_t s_item;
   const InstDesc* d = descs_of(h);
   const uint32_t k = h->k;
+  // CTA b starts with item b (CTAs beyond the items leave at once); the
+  // counter hands out the rest, counting from the grid size
+  const uint32_t total = ld_cg(&h->total_items);
+  if (blockIdx.x >= total) return;
   ulonglong2* my_rows = s_acc + threadIdx.x;
   const uint32_t rs = blockDim.x;
   for (uint32_t r = 0; r < rmax; r++) my_rows[r * rs] = make_ulonglong2(0, 0);
   uint32_t cur = kNoneU32;
   ApplyLane l{};
-  const uint32_t total = ld_cg(&h->total_items);
-  for (;;) {
-    if (threadIdx.x == 0) s_item = atomicAdd(&h->next_item, 1u);
-    __syncthreads();
-    const uint32_t it = s_item;
-    if (it >= total) break;
+  for (uint32_t it = blockIdx.x; it < total;) {
     const uint32_t j = inst_of_item(d, k, it);
     const InstDesc& g = d[j];
     if (j != cur) {
@@ -191,13 +190,17 @@ __global__ void k_apply_m(BatchHead* __restrict__ h, uint32_t rmax, uint32_t ite
         apply_direct<true>(l, g.sketch, g.V, g.W, g.rec + item.y, g.recw + item.y, item.z - item.y, g.D, s_xp, s_w);
       else
         apply_direct<false>(l, g.sketch, g.V, g.W, g.rec + item.y, g.recw + item.y, item.z - item.y, g.D, s_xp, s_w);
-      continue;
+    } else {
+      ulonglong2* gb = g.sketch + ((size_t)l.layer * g.V + item.x) * g.W + l.jbase;
+      if (g.D > 32)
+        apply_item<true>(l, gb, g.rec + item.y, item.z - item.y, item.w != 0, g.D, g.R, s_xp, my_rows, rs);
+      else
+        apply_item<false>(l, gb, g.rec + item.y, item.z - item.y, item.w != 0, g.D, g.R, s_xp, my_rows, rs);
     }
-    ulonglong2* gb = g.sketch + ((size_t)l.layer * g.V + item.x) * g.W + l.jbase;
-    if (g.D > 32)
-      apply_item<true>(l, gb, g.rec + item.y, item.z - item.y, item.w != 0, g.D, g.R, s_xp, my_rows, rs);
-    else
-      apply_item<false>(l, gb, g.rec + item.y, item.z - item.y, item.w != 0, g.D, g.R, s_xp, my_rows, rs);
+    // both item paths end with __syncthreads: every thread has read s_item
+    if (threadIdx.x == 0) s_item = gridDim.x + atomicAdd(&h->next_item, 1u);
+    __syncthreads();
+    it = s_item;
   }
 }
 

@@ -35,6 +35,9 @@ constexpr uint32_t kDefaultItemRecords = 256;
 constexpr uint32_t kMinItemRecords = 64;
 // Most vertex slices of the update's plan kernels.
 constexpr uint32_t kPlanSlices = 1024;
+// Most CTAs of the single-graph apply kernel (its direct-path items number
+// at most 2 per CTA + 1 beyond one per 64 direct records).
+constexpr uint32_t kPlanGridCap = 8192;
 // Dynamic shared memory of an apply CTA: staged records {idx, pre(idx)},
 // rows x threads fold rows, and the records' vertices (direct path).
 inline size_t apply_smem_bytes(uint32_t item_records, uint32_t rows, uint32_t threads) {
@@ -73,6 +76,7 @@ enum : uint32_t {
   GC_NBIG = 17,      // members of big components this round
   GC_NDIRECT = 18,   // direct-path records of the current chunk
   GC_NLIVE = 19,     // live components of the next recovery round
+  GC_REC_DIRTY = 20, // a recovery gave up at a barrier: its scratch may be non-zero
   GC_SLOTS = 32
 };
 

@@ -19,7 +19,8 @@ constexpr uint32_t kMaxEdges = CUPC_STATIC_MAX_EDGES;
 constexpr uint32_t kMaxKeys = 64 * 8;
 constexpr size_t kAlignS = 256;
 constexpr size_t align_s(size_t x) { return (x + kAlignS - 1) / kAlignS * kAlignS; }
-constexpr size_t kMaxItems = 4ull * kMaxEdges / kMinItemRecords + (kMaxV < 2ull * kMaxEdges ? kMaxV : 2ull * kMaxEdges) + 1;
+constexpr size_t kMaxItems =
+    4ull * kMaxEdges / kMinItemRecords + (kMaxV < 2ull * kMaxEdges ? kMaxV : 2ull * kMaxEdges) + 2ull * kPlanGridCap + 1;
 // byte offsets inside the static scratch
 constexpr size_t kOffGc = 0;
 constexpr size_t kOffKeys = align_s(kOffGc + GC_SLOTS * sizeof(uint32_t));

@@ -65,6 +65,7 @@ __device__ __forceinline__ bool grid_barrier(uint32_t* gc, uint32_t nblocks, uin
         }
         if (t - t0 > limit_ns) {
           atomicOr(&gc[GC_ERR], kErrTimeout);
+          atomicOr(&gc[GC_REC_DIRTY], 1u);
           ok = 0;
           break;
         }
@@ -343,6 +344,9 @@ __global__ void __launch_bounds__(kRecThreads, 2) k_recover(RecArgs a) {
 #define CUPC_GRID_SYNC() \
   if (!grid_barrier(gc, nb, epoch, &s_ok)) return
 
+  // after a recovery that gave up at a barrier, the reduce accumulators and
+  // the last-arriver counters may hold partial sums: clear them first
+  const bool dirty = ld_cg(&gc[GC_REC_DIRTY]) != 0;
   for (uint32_t w = gtid; w < V; w += gstride) {
     a.label[w] = w;
     a.final_[w] = 0;
@@ -353,7 +357,10 @@ __global__ void __launch_bounds__(kRecThreads, 2) k_recover(RecArgs a) {
     a.best0[w] = kNone;
     a.best1[w] = kNone;
     a.rcnt[w] = 0;
+    if (dirty) a.pcount[w] = 0;
   }
+  if (dirty)
+    for (size_t i = gtid; i < (size_t)V * W; i += gstride) a.acc[i] = make_ulonglong2(0, 0);
   if (gtid == 0) {
     gc[GC_NFOREST] = 0;
     gc[GC_NFAIL] = 0;
@@ -373,6 +380,7 @@ __global__ void __launch_bounds__(kRecThreads, 2) k_recover(RecArgs a) {
     a.log_ncand[r] = 0;
   }
   CUPC_GRID_SYNC();
+  if (dirty && gtid == 0) gc[GC_REC_DIRTY] = 0;  // every CTA has read it
 
   for (uint32_t r = 0; r < a.L; r++) {
     const uint64_t kchk = a.keys[r * (a.C + 1) + a.C];

@@ -93,7 +93,7 @@ __global__ void __launch_bounds__(256) k_plan_count(const uint32_t* __restrict__
 // share of the direct items. Resets cnt for the next chunk.
 __global__ void __launch_bounds__(256) k_plan_write(uint32_t* cnt, uint32_t* cursor, uint4* items, uint32_t V,
                                                     uint32_t vpt, uint32_t item_records, const uint4* __restrict__ part,
-                                                    uint32_t* gc) {
+                                                    uint32_t apply_ctas, uint32_t* gc) {
   __shared__ uint32_t sw[3][32];
   if (ld_cg(&gc[GC_ERR]) & kErrInval) return;
   const uint32_t nb = gridDim.x, b = blockIdx.x;
@@ -140,9 +140,12 @@ __global__ void __launch_bounds__(256) k_plan_write(uint32_t* cnt, uint32_t* cur
 #pragma unroll
     for (int k = 0; k < 3; k++) carry[k] += t[k];
   }
-  const uint32_t ndi = (nd + kDirectItemRecords - 1) / kDirectItemRecords;
+  // direct items: about two per apply CTA, of kDirectItemMin..kDirectItemRecords
+  // records (so at most max(2 * apply_ctas + 1, nd / kDirectItemRecords + 1))
+  const uint32_t dsz = min(kDirectItemRecords, max(kDirectItemMin, (nd + 2 * apply_ctas - 1) / (2 * apply_ctas)));
+  const uint32_t ndi = (nd + dsz - 1) / dsz;
   for (uint32_t q = b * blockDim.x + threadIdx.x; q < ndi; q += nb * blockDim.x)
-    items[nfold + q] = make_uint4(kDirectItem, q * kDirectItemRecords, min(nd, (q + 1) * kDirectItemRecords), 0u);
+    items[nfold + q] = make_uint4(kDirectItem, q * dsz, min(nd, (q + 1) * dsz), 0u);
   if (b == 0 && threadIdx.x == 0) {
     gc[GC_NITEMS] = nfold + ndi;
     gc[GC_NDIRECT] = nd;
@@ -187,24 +190,29 @@ __global__ void k_apply(ulonglong2* __restrict__ sketch, const uint64_t* __restr
   __shared__ uint32_t s_item;
 
   if (ld_cg(&gc[GC_ERR]) & kErrInval) return;
+  // CTA b starts with item b; CTAs beyond the items leave before touching
+  // the item counter (a small batch would otherwise have every CTA of the
+  // grid queue on one address); a CTA that finishes takes the next item
+  // from the counter, which counts from the grid size
+  const uint32_t nitems = ld_cg(&gc[GC_NITEMS]);
+  if (blockIdx.x >= nitems) return;
   const ApplyLane l = apply_lane(keys, L, C, D, P, R);
   ulonglong2* my_rows = s_acc + threadIdx.x;
   const uint32_t rs = blockDim.x;
   for (uint32_t d = 0; d < R; d++) my_rows[d * rs] = make_ulonglong2(0, 0);
 
-  const uint32_t nitems = ld_cg(&gc[GC_NITEMS]);
-  for (;;) {
-    if (threadIdx.x == 0) s_item = atomicAdd(&gc[GC_NEXT_ITEM], 1u);
-    __syncthreads();
-    const uint32_t it = s_item;
-    if (it >= nitems) break;
+  for (uint32_t it = blockIdx.x; it < nitems;) {
     const uint4 item = items[it];
     if (item.x == kDirectItem) {
       apply_direct<kWide>(l, sketch, V, W, rec + item.y, recw + item.y, item.z - item.y, D, s_xp, s_w);
-      continue;
+    } else {
+      ulonglong2* gb = sketch + ((size_t)l.layer * V + item.x) * W + l.jbase;
+      apply_item<kWide>(l, gb, rec + item.y, item.z - item.y, item.w != 0, D, R, s_xp, my_rows, rs);
     }
-    ulonglong2* gb = sketch + ((size_t)l.layer * V + item.x) * W + l.jbase;
-    apply_item<kWide>(l, gb, rec + item.y, item.z - item.y, item.w != 0, D, R, s_xp, my_rows, rs);
+    // both item paths end with __syncthreads: every thread has read s_item
+    if (threadIdx.x == 0) s_item = gridDim.x + atomicAdd(&gc[GC_NEXT_ITEM], 1u);
+    __syncthreads();
+    it = s_item;
   }
 }
 
@@ -251,17 +259,18 @@ cudaError_t configure_apply(cupc_graph* g) {
 
 cudaError_t launch_update_chunk(cupc_graph* g, const uint32_t* edges, size_t n, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
+  const int agrid = (int)std::min<size_t>(std::min<size_t>((size_t)g->apply_grid, 2 * n), kPlanGridCap);
   int grid = (int)std::min<size_t>((n + 255) / 256, (size_t)g->sms * 8);
   {
     ProfScope ps(g, s, PC_GROUP, 4);
     k_count<<<grid, 256, 0, s>>>(edges, n, g->cnt, g->gc);
     const uint32_t vpt = plan_vpt(g->V), nb = (g->V + 256 * vpt - 1) / (256 * vpt);
     k_plan_count<<<nb, 256, 0, s>>>(g->cnt, g->V, vpt, g->item_records, g->part, g->gc);
-    k_plan_write<<<nb, 256, 0, s>>>(g->cnt, g->cursor, g->items, g->V, vpt, g->item_records, g->part, g->gc);
+    k_plan_write<<<nb, 256, 0, s>>>(g->cnt, g->cursor, g->items, g->V, vpt, g->item_records, g->part,
+                                    (uint32_t)agrid, g->gc);
     k_scatter<<<grid, 256, 0, s>>>(edges, n, g->V, g->cursor, g->rec, g->recw, g->gc);
   }
   ProfScope ps(g, s, PC_APPLY, 1);
-  int agrid = (int)std::min<size_t>((size_t)g->apply_grid, 2 * n);
   auto kern = g->D > 32 ? k_apply<true> : k_apply<false>;
   kern<<<agrid, g->apply_threads, g->apply_smem, s>>>(g->sketch, g->keys, g->rec, g->recw, g->items, g->gc, g->V,
                                                        g->L, g->C, g->D, g->W, g->P, g->R, g->item_records);

@@ -52,7 +52,8 @@ constexpr uint32_t kDirectMax = 2;
 // Work item whose records belong to several direct-path vertices, and its
 // size: small, so that a sparse batch still spreads over every SM.
 constexpr uint32_t kDirectItem = 0xFFFFFFFFu;
-constexpr uint32_t kDirectItemRecords = 64;
+constexpr uint32_t kDirectItemRecords = 64;  // at most; the single-graph plan
+constexpr uint32_t kDirectItemMin = 16;      // sizes them to the apply grid
 
 // Work plan of one batch, run by one CTA: vertices with more than
 // kDirectMax records ("fold" vertices) get record segments after all direct
