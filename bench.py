@@ -403,7 +403,7 @@ def batching_compare(torch, C, dev, stream, n_batches=48, rounds=30):
     V = 1 << 17
     st, g = C.cupc_init(V, 1, (0, 0, 0, 4 << 20), None, stream)
     C.check(st)
-    AT.apply(g, V, int(np.median(sizes)))
+    AT.apply_buckets(g, V)  # each batch with the setting of its size
 
     def plain():
         for i in range(n_batches):

@@ -245,6 +245,13 @@ void cupc_server_destroy(cupc_server* s);
  * in use}. */
 cupc_status cupc_set_tuning(cupc_graph* g, uint32_t item_records, uint32_t smem_rows, uint32_t ctas_per_sm);
 cupc_status cupc_get_tuning(const cupc_graph* g, uint32_t* out4);
+/* The same tunables for one batch-size bucket only: a chunk of n edges uses
+ * bucket floor(log4 n) (5 for n < 4^6, 15 for n >= 4^15) if it was set,
+ * else the graph's setting above, so that one graph can run small and large
+ * batches each with its own setting. bucket in 5..15; all three tunables 0
+ * clear the bucket. CUPC_EINVAL when out of range. */
+cupc_status cupc_set_tuning_bucket(cupc_graph* g, uint32_t bucket, uint32_t item_records, uint32_t smem_rows,
+                                   uint32_t ctas_per_sm);
 
 /* Derived parameters of a graph: out4 = {L, C, D, W}. */
 cupc_status cupc_get_params(const cupc_graph* g, uint32_t* out4);

@@ -9,8 +9,9 @@ records a vertex receives per batch, i.e. on V and the batch size.
 tune() times every candidate setting on the device (CUDA events recorded by
 the library around each apply launch) for each batch-size bucket (powers of
 four edges) and keeps the fastest; the table is stored as JSON keyed by GPU
-name and graph shape. apply() picks the bucket of a batch and sets it on a
-graph. Run `python -m paper_2509_14433_gb300.autotune --V 16384` on the
+name and graph shape. apply() sets the setting of one batch size as a
+graph's default; apply_buckets() gives the graph every bucket's setting, and
+the library then picks one per batch by its size. Run `python -m paper_2509_14433_gb300.autotune --V 16384` on the
 target GPU to (re)write the table.
 """
 from __future__ import annotations
@@ -81,6 +82,27 @@ def apply(g, V: int, n_edges: int, table: dict | None = None) -> bool:
     if s is None:
         return False
     return C.cupc_set_tuning(g, *s) == C.CUPC_OK
+
+
+def apply_buckets(g, V: int, table: dict | None = None) -> int:
+    """Set every tuned batch-size bucket of this GPU and graph shape on
+    graph handle g (cupc_set_tuning_bucket), so that each batch runs with
+    the setting of its own size. Returns the number of buckets set."""
+    from . import cupc as C
+    try:
+        import torch
+        name = torch.cuda.get_device_name(0)
+    except Exception:
+        return 0
+    p = np.zeros(4, np.uint32)
+    C.cupc_get_params(g, p)
+    L, Cc, D, _ = (int(x) for x in p)
+    ent = (load() if table is None else table).get(name, {}).get(shape_key(V, L, Cc, D), {})
+    k = 0
+    for b, e in ent.items():
+        if 5 <= int(b) <= 15 and C.cupc_set_tuning_bucket(g, int(b), *e["setting"]) == C.CUPC_OK:
+            k += 1
+    return k
 
 
 def _time_setting(C, g, e_d, o_d, n, reps, setting):

@@ -506,6 +506,27 @@ cupc_status cupc_set_tuning(cupc_graph* g, uint32_t item_records, uint32_t smem_
   return CUPC_OK;
 }
 
+cupc_status cupc_set_tuning_bucket(cupc_graph* g, uint32_t bucket, uint32_t item_records, uint32_t smem_rows,
+                                   uint32_t ctas_per_sm) {
+  if (!g || bucket < 5 || bucket > 15) return CUPC_EINVAL;
+  cupc_graph::ApplyTune& t = g->tune_b[bucket];
+  if (item_records == 0 && smem_rows == 0 && ctas_per_sm == 0) {  // back to the default
+    t.set = false;
+    return CUPC_OK;
+  }
+  if (item_records == 0) item_records = kDefaultItemRecords;
+  if (smem_rows == 0) smem_rows = g->D < kSmemRows ? g->D : kSmemRows;
+  if (item_records < kMinItemRecords || item_records > kItemRecords || smem_rows > kSmemRowsMax || smem_rows > g->D)
+    return CUPC_EINVAL;
+  int smem = 0, grid = 0;
+  if (apply_config(g, item_records, smem_rows, ctas_per_sm, &smem, &grid) != cudaSuccess) {
+    cudaGetLastError();
+    return CUPC_EINVAL;
+  }
+  t = cupc_graph::ApplyTune{true, item_records, smem_rows, ctas_per_sm, smem, grid};
+  return CUPC_OK;
+}
+
 cupc_status cupc_get_tuning(const cupc_graph* g, uint32_t* out4) {
   if (!g || !out4) return CUPC_EINVAL;
   out4[0] = g->item_records;

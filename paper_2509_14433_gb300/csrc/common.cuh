@@ -122,6 +122,12 @@ struct cupc_graph {
   int device, sms;
   int apply_threads, apply_smem, apply_grid;
   uint32_t item_records, apply_cps;  // tunables: records per work item, CTAs per SM (0 = max)
+  // optional per-batch-size settings: bucket floor(log4 edges) (at least 5)
+  struct ApplyTune {
+    bool set;
+    uint32_t item_records, R, cps;
+    int smem, grid;
+  } tune_b[16];
   int rec_grid;
   // sketches and keys
   ulonglong2* sketch;  // L*V*W
@@ -213,6 +219,13 @@ cudaError_t launch_update_chunk(cupc_graph* g, const uint32_t* edges, size_t n, 
 cudaError_t launch_validate(cupc_graph* g, const uint32_t* edges, const int8_t* ops, size_t n, cudaStream_t s);
 cudaError_t setup_update(cupc_graph* g);
 cudaError_t configure_apply(cupc_graph* g);
+cudaError_t apply_config(const cupc_graph* g, uint32_t item_records, uint32_t R, uint32_t cps, int* smem, int* grid);
+// Tuning bucket of a batch of n edges: floor(log4 n), at least 5, at most 15.
+inline uint32_t tune_bucket(size_t n) {
+  uint32_t b = 5;
+  while (b < 15 && ((size_t)1 << (2 * (b + 1))) <= n) b++;
+  return b;
+}
 cudaError_t raise_apply_smem_limit(int bytes);
 cudaError_t setup_recover(cupc_graph* g);
 cudaError_t launch_recover(cupc_graph* g, cudaStream_t s);

@@ -72,7 +72,7 @@ cudaError_t device_setup(int dev, DeviceSetup** out) {
     if (s.err == cudaSuccess) s.err = cudaDeviceGetAttribute(&s.sms, cudaDevAttrMultiProcessorCount, dev);
     if (s.err == cudaSuccess) {
       // the widest apply launch: V = kMaxV sets the most layers
-      cupc_graph g;
+      cupc_graph g{};
       fill_dims(g, kMaxV);
       g.sms = s.sms;
       s.err = setup_update(&g);
@@ -100,7 +100,7 @@ extern "C" cupc_status cupc_update_sketch_static(void* sketch, uint32_t V, uint6
   if (device_setup(dev, &ds) != cudaSuccess) return CUPC_ECUDA;
   cudaStream_t s = (cudaStream_t)stream;
 
-  cupc_graph g;
+  cupc_graph g{};
   fill_dims(g, V);
   g.seed = seed;
   g.max_batch = kMaxEdges;

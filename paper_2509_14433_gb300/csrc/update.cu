@@ -242,38 +242,52 @@ cudaError_t setup_update(cupc_graph* g) {
   return configure_apply(g);
 }
 
-// Shared memory and persistent grid of k_apply for the current tunables.
-cudaError_t configure_apply(cupc_graph* g) {
-  g->apply_smem = (int)apply_smem_bytes(g->item_records, g->R, (uint32_t)g->apply_threads);
-  cudaError_t e = raise_apply_smem_limit(g->apply_smem);
+// Shared memory and persistent grid of k_apply for the given tunables.
+cudaError_t apply_config(const cupc_graph* g, uint32_t item_records, uint32_t R, uint32_t cps, int* smem, int* grid) {
+  *smem = (int)apply_smem_bytes(item_records, R, (uint32_t)g->apply_threads);
+  cudaError_t e = raise_apply_smem_limit(*smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, g->D > 32 ? k_apply<true> : k_apply<false>,
-                                                    g->apply_threads, g->apply_smem);
+                                                    g->apply_threads, *smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
-  if (g->apply_cps && (int)g->apply_cps < per_sm) per_sm = (int)g->apply_cps;
-  g->apply_grid = per_sm * g->sms;
+  if (cps && (int)cps < per_sm) per_sm = (int)cps;
+  *grid = per_sm * g->sms;
   return cudaSuccess;
+}
+
+// ... and for the graph's default tunables.
+cudaError_t configure_apply(cupc_graph* g) {
+  return apply_config(g, g->item_records, g->R, g->apply_cps, &g->apply_smem, &g->apply_grid);
 }
 
 cudaError_t launch_update_chunk(cupc_graph* g, const uint32_t* edges, size_t n, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
-  const int agrid = (int)std::min<size_t>(std::min<size_t>((size_t)g->apply_grid, 2 * n), kPlanGridCap);
+  // the setting of this batch size's bucket, else the graph's default
+  uint32_t ir = g->item_records, R = g->R;
+  int smem = g->apply_smem, grid_max = g->apply_grid;
+  const cupc_graph::ApplyTune& t = g->tune_b[tune_bucket(n)];
+  if (t.set) {
+    ir = t.item_records;
+    R = t.R;
+    smem = t.smem;
+    grid_max = t.grid;
+  }
+  const int agrid = (int)std::min<size_t>(std::min<size_t>((size_t)grid_max, 2 * n), kPlanGridCap);
   int grid = (int)std::min<size_t>((n + 255) / 256, (size_t)g->sms * 8);
   {
     ProfScope ps(g, s, PC_GROUP, 4);
     k_count<<<grid, 256, 0, s>>>(edges, n, g->cnt, g->gc);
     const uint32_t vpt = plan_vpt(g->V), nb = (g->V + 256 * vpt - 1) / (256 * vpt);
-    k_plan_count<<<nb, 256, 0, s>>>(g->cnt, g->V, vpt, g->item_records, g->part, g->gc);
-    k_plan_write<<<nb, 256, 0, s>>>(g->cnt, g->cursor, g->items, g->V, vpt, g->item_records, g->part,
-                                    (uint32_t)agrid, g->gc);
+    k_plan_count<<<nb, 256, 0, s>>>(g->cnt, g->V, vpt, ir, g->part, g->gc);
+    k_plan_write<<<nb, 256, 0, s>>>(g->cnt, g->cursor, g->items, g->V, vpt, ir, g->part, (uint32_t)agrid, g->gc);
     k_scatter<<<grid, 256, 0, s>>>(edges, n, g->V, g->cursor, g->rec, g->recw, g->gc);
   }
   ProfScope ps(g, s, PC_APPLY, 1);
   auto kern = g->D > 32 ? k_apply<true> : k_apply<false>;
-  kern<<<agrid, g->apply_threads, g->apply_smem, s>>>(g->sketch, g->keys, g->rec, g->recw, g->items, g->gc, g->V,
-                                                       g->L, g->C, g->D, g->W, g->P, g->R, g->item_records);
+  kern<<<agrid, g->apply_threads, smem, s>>>(g->sketch, g->keys, g->rec, g->recw, g->items, g->gc, g->V, g->L, g->C,
+                                              g->D, g->W, g->P, R, ir);
   return cudaGetLastError();
 }
 

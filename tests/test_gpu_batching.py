@@ -128,7 +128,21 @@ def test_every_tuning_gives_identical_sketches():
         assert tuple(int(x) for x in out[:3]) == setting
         assert dev.update(E) == 0
         assert np.array_equal(dev.export(), want), setting
+    # per-bucket settings: batches of 1k, 5k and 20k edges each take their
+    # own bucket's setting (5, 6, 7); the default serves the rest
     dev = _dev(V, 8)
+    for b, setting in ((5, (64, 4, 1)), (6, (512, 16, 0)), (7, (128, 12, 3))):
+        assert C.cupc_set_tuning_bucket(dev.h, b, *setting) == 0
+    assert C.cupc_set_tuning_bucket(dev.h, 8, 0, 0, 0) == 0  # cleared: the default
+    i = 0
+    for n in (1000, 5000, 20000, 3, 1 << 12):
+        assert dev.update(E[i:i + n]) == 0
+        i += n
+    assert dev.update(E[i:]) == 0
+    assert np.array_equal(dev.export(), want)
+    assert C.cupc_set_tuning_bucket(dev.h, 4, 64, 8, 0) == C.CUPC_EINVAL
+    assert C.cupc_set_tuning_bucket(dev.h, 16, 64, 8, 0) == C.CUPC_EINVAL
+    assert C.cupc_set_tuning_bucket(dev.h, 6, 32, 8, 0) == C.CUPC_EINVAL
     assert C.cupc_set_tuning(dev.h, 32, 12, 0) == C.CUPC_EINVAL  # records per item below 64
     assert C.cupc_set_tuning(dev.h, 512, 17, 0) == C.CUPC_EINVAL  # more than 16 shared rows
     assert AT.bucket_of(1000) == 5 and AT.bucket_of(4096) == 6 and AT.bucket_of(1 << 20) == 10
