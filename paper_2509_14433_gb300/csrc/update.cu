@@ -59,6 +59,65 @@ __global__ void k_count(const uint32_t* __restrict__ edges, size_t n, uint32_t* 
   }
 }
 
+// Dense batches on small graphs (V <= kPrivMaxV, at least kPrivPerVertex
+// records per vertex on average): each CTA takes a contiguous slice of the
+// batch and counts its endpoints in a shared histogram of all V vertices, so
+// the global counters see one atomic per (CTA, vertex) instead of one per
+// record.
+__global__ void __launch_bounds__(1024) k_count_priv(const uint32_t* __restrict__ edges, size_t n, uint32_t V,
+                                                     uint32_t* cnt, const uint32_t* gc) {
+  extern __shared__ uint32_t s_h[];  // V
+  if (ld_cg(&gc[GC_ERR]) & kErrInval) return;
+  for (uint32_t w = threadIdx.x; w < V; w += blockDim.x) s_h[w] = 0;
+  __syncthreads();
+  const size_t chunk = (n + gridDim.x - 1) / gridDim.x, lo = blockIdx.x * chunk, hi = min(n, lo + chunk);
+  for (size_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+    atomicAdd(&s_h[edges[2 * i]], 1u);
+    atomicAdd(&s_h[edges[2 * i + 1]], 1u);
+  }
+  __syncthreads();
+  for (uint32_t w = threadIdx.x; w < V; w += blockDim.x) {
+    const uint32_t c = s_h[w];
+    if (c) atomicAdd(&cnt[w], c);
+  }
+}
+
+// ... and groups them: the CTA counts its slice again, reserves one range of
+// each of its vertices' segments (one atomic per vertex), then places each
+// record at the range start + its rank in shared memory. Records of a vertex
+// land in a different order than with k_scatter; XOR does not see order.
+__global__ void __launch_bounds__(1024) k_scatter_priv(const uint32_t* __restrict__ edges, size_t n, uint32_t V,
+                                                       uint32_t* cursor, uint64_t* __restrict__ rec,
+                                                       uint32_t* __restrict__ recw, const uint32_t* gc) {
+  extern __shared__ uint32_t s_h[];  // V counts, then V range starts
+  uint32_t* s_base = s_h + V;
+  if (ld_cg(&gc[GC_ERR]) & kErrInval) return;
+  const uint32_t nd = ld_cg(&gc[GC_NDIRECT]);
+  for (uint32_t w = threadIdx.x; w < V; w += blockDim.x) s_h[w] = 0;
+  __syncthreads();
+  const size_t chunk = (n + gridDim.x - 1) / gridDim.x, lo = blockIdx.x * chunk, hi = min(n, lo + chunk);
+  for (size_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+    atomicAdd(&s_h[edges[2 * i]], 1u);
+    atomicAdd(&s_h[edges[2 * i + 1]], 1u);
+  }
+  __syncthreads();
+  for (uint32_t w = threadIdx.x; w < V; w += blockDim.x) {
+    const uint32_t c = s_h[w];
+    if (c) s_base[w] = atomicAdd(&cursor[w], c);
+    s_h[w] = 0;
+  }
+  __syncthreads();
+  for (size_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+    const uint32_t u = edges[2 * i], v = edges[2 * i + 1];
+    const uint64_t idx = (uint64_t)min(u, v) * V + max(u, v);
+    const uint32_t pu = s_base[u] + atomicAdd(&s_h[u], 1u), pv = s_base[v] + atomicAdd(&s_h[v], 1u);
+    rec[pu] = idx;
+    rec[pv] = idx;
+    if (pu < nd) recw[pu] = u;
+    if (pv < nd) recw[pv] = v;
+  }
+}
+
 // Work plan of one chunk over many CTAs, in two launches that never wait on
 // one another. The vertices are cut into slices of 256 * vpt; slice b is
 // planned by CTA b. Kinds of vertices and the layout of records and items
@@ -233,6 +292,11 @@ cudaError_t raise_apply_smem_limit(int bytes) {
 }
 
 cudaError_t setup_update(cupc_graph* g) {
+  // the shared histograms of the dense-batch grouping (fixed maximum sizes)
+  cudaError_t e = cudaFuncSetAttribute(k_count_priv, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * kPrivMaxV);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_scatter_priv, cudaFuncAttributeMaxDynamicSharedMemorySize, 8 * kPrivMaxV);
+  if (e != cudaSuccess) return e;
   g->P = 1;
   while (g->P < g->C + 1) g->P <<= 1;
   g->R = g->D < kSmemRows ? g->D : kSmemRows;
@@ -278,11 +342,20 @@ cudaError_t launch_update_chunk(cupc_graph* g, const uint32_t* edges, size_t n, 
   int grid = (int)std::min<size_t>((n + 255) / 256, (size_t)g->sms * 8);
   {
     ProfScope ps(g, s, PC_GROUP, 4);
-    k_count<<<grid, 256, 0, s>>>(edges, n, g->cnt, g->gc);
+    // dense batch on a small graph: group through shared histograms
+    const int pgrid = (int)std::min<size_t>((size_t)g->sms, 2 * n / ((size_t)kPrivPerVertex * g->V));
+    const bool priv = g->V <= kPrivMaxV && pgrid >= (int)kPrivMinCtas;
+    if (priv)
+      k_count_priv<<<pgrid, 1024, 4 * g->V, s>>>(edges, n, g->V, g->cnt, g->gc);
+    else
+      k_count<<<grid, 256, 0, s>>>(edges, n, g->cnt, g->gc);
     const uint32_t vpt = plan_vpt(g->V), nb = (g->V + 256 * vpt - 1) / (256 * vpt);
     k_plan_count<<<nb, 256, 0, s>>>(g->cnt, g->V, vpt, ir, g->part, g->gc);
     k_plan_write<<<nb, 256, 0, s>>>(g->cnt, g->cursor, g->items, g->V, vpt, ir, g->part, (uint32_t)agrid, g->gc);
-    k_scatter<<<grid, 256, 0, s>>>(edges, n, g->V, g->cursor, g->rec, g->recw, g->gc);
+    if (priv)
+      k_scatter_priv<<<pgrid, 1024, 8 * g->V, s>>>(edges, n, g->V, g->cursor, g->rec, g->recw, g->gc);
+    else
+      k_scatter<<<grid, 256, 0, s>>>(edges, n, g->V, g->cursor, g->rec, g->recw, g->gc);
   }
   ProfScope ps(g, s, PC_APPLY, 1);
   auto kern = g->D > 32 ? k_apply<true> : k_apply<false>;
