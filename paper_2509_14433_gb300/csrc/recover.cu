@@ -6,21 +6,27 @@
 // The whole recovery is one cooperative launch: every CTA is co-resident, and
 // the phases of a round are separated by a grid barrier whose wait is bounded
 // (on expiry it sets the timeout error and every CTA returns). Round r:
-//   reset       per-round scratch
-//   group       live vertices grouped by component label (count, tile scan,
-//               scatter); round 0 skips it: every vertex is its own component
-//   reduce      spans of kRecSpan members: thread t XORs bucket t of layer r of
-//               each member (coalesced 16-byte loads); a component that lies
-//               inside one span is sampled in place, others are XORed into a
-//               per-component accumulator and sampled after the barrier
-//   sample      ZERO / GOOD(edge) / FAIL, first good bucket in index order
+//   group       live vertices grouped by component label (count, segment
+//               offsets, scatter); round 0 skips it: every vertex is its own
+//               component
+//   reduce      components of at most kRecSpan members: a warp per span,
+//               lane l XORs buckets l + 32q of layer r of each member; bigger
+//               ones in CTA tiles sized to the grid, thread t XORs bucket t.
+//               A component inside one span or tile is sampled in place; one
+//               over several is XORed into its accumulator and sampled by the
+//               last span or tile to finish
+//   sample      ZERO / GOOD(edge) / FAIL, first good bucket in index order;
+//               32 samples of a warp are booked at once
 //   hook        minimum spanning forest (weights = edge ids) of the candidate
-//               edges over the round-start components: parallel Boruvka with
-//               min-id edges and pointer jumping, which adds exactly the edges
-//               Kruskal in ascending id order would
+//               edges over the round-start components: grid-wide Boruvka
+//               steps with min-id edges until at most kSmallHook candidates
+//               still cross two trees, then one CTA finishes in shared
+//               memory; it adds exactly the edges Kruskal in ascending id
+//               order would
 //   relabel     every vertex takes the minimum vertex id of its component
 // A component whose merged sketch is ZERO has an empty cut; it is not sampled
-// again until it changes.
+// again until it changes. With one live component left its merged sketch is
+// zero by linearity, so the round is logged without reading its layer.
 #include "common.cuh"
 
 namespace cupc {

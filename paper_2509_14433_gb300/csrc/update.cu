@@ -2,17 +2,23 @@
 // Algorithm": an update of edge (u,v) updates every sketch of u and of v;
 // Theorem A.2: CameoSketch touches one bucket per column per update).
 //
-// One chunk of <= max_batch edges goes through four stream-ordered kernels:
-//   k_count   per-vertex record counts (2 records per edge, one per endpoint)
+// One chunk of <= max_batch edges (validated first by k_validate) goes
+// through five stream-ordered kernels:
+//   k_count   per-vertex record counts (2 records per edge, one per
+//             endpoint); k_count_priv for dense batches on small graphs,
+//             through per-CTA shared histograms
 //   k_plan_count / k_plan_write
 //             exclusive scan over vertex slices -> per-vertex cursors and
-//             work items of at most item_records records of one vertex
+//             work items: at most item_records records of one vertex, or
+//             16..64 records of vertices with at most 2 (the direct path)
 //   k_scatter endpoint records (the edge index u*V+v) grouped by vertex
-//   k_apply   persistent CTAs pull work items; thread (layer r, slot s)
-//             hashes every record of the item for column s of layer r (slot
-//             C computes the checksum and owns the deterministic bucket),
-//             folds them in shared memory, then read-modify-writes only the
-//             touched buckets of that vertex in HBM with 16-byte accesses.
+//             (k_scatter_priv with k_count_priv)
+//   k_apply   persistent CTAs, CTA b starting on item b; thread (layer r,
+//             slot s) hashes every record of the item for column s of layer
+//             r (slot C computes the checksum and owns the deterministic
+//             bucket), folds them in shared memory, then read-modify-writes
+//             only the touched buckets of that vertex in HBM with 16-byte
+//             accesses; direct items XOR each bucket straight into HBM.
 // XOR is associative and commutative, so the result is bit-identical to
 // applying the updates one by one in stream order.
 #include "update_dev.cuh"
