@@ -291,7 +291,7 @@ def run_gpu(args):
     torch.cuda.synchronize()
     barrier()
     t0 = time.perf_counter()
-    e2e_steps = max(1, min(args.steps, 3))
+    e2e_steps = max(3, min(args.steps, 5))  # at least 3: one slow step must not set the number
     for _ in range(e2e_steps):
         nf_h = step_host()
     torch.cuda.synchronize()
