@@ -320,6 +320,7 @@ def run_gpu(args):
 
     # ---- plain V=1024 toggle stream: updates/s and query latency
     plain = plain_stream_latency(torch, C, dev, stream)
+    pstream = None if args.no_batching else paper_stream(torch, C, dev, stream)
     batching = None if args.no_batching else batching_compare(torch, C, dev, stream)
     serving = None if args.no_serving else serving_compare(torch, C, dev)
 
@@ -367,6 +368,7 @@ def run_gpu(args):
                              "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst copy)" if peaks else "fallback"},
                 "kernel_time_share": shares,
                 "batch_size_vs_query_latency": sweep,
+                "paper_stream_shape": pstream,
                 "query_latency_us": {"dense_after_batch_p50": statistics.median(lat_dense),
                                      "dense_after_batch_p99": float(np.percentile(lat_dense, 99)),
                                      **plain},
@@ -570,6 +572,65 @@ def serving_compare(torch, C, dev, n_graphs=64, upd_range=(5e4, 5e5), seed=5):
         for g in graphs:
             C.cupc_destroy(g)
     return out
+
+
+def paper_stream(torch, C, dev, stream, n_upd=1 << 21):
+    """The paper's stream shape on a K13-sized dense graph (context for its
+    published numbers, not the headline workload): V = 2^13, ER(0.5) edges
+    (about the K13 density) in a seeded random order, inserted one burst of
+    rho ~ U[1000, 2000] updates at a time, each followed by rho/9 uniform
+    Connected pairs (10% of the operations are queries). The first n_upd
+    updates of the standard stream (insert all, then delete all) are run:
+    updates/s and queries/s over the whole prefix, and the latency of a
+    sampled burst's query (host submit -> answers ready, recovery
+    included)."""
+    V, g_rng = 1 << 13, WL.rng(13)
+    E = WL.er_edges(V, 0.5, 13)
+    E = E[g_rng.permutation(len(E))][:n_upd]
+    bursts = []
+    i = 0
+    while i < len(E):
+        rho = int(g_rng.integers(1000, 2001))
+        bursts.append((i, min(rho, len(E) - i), max(1, rho // 9)))
+        i += rho
+    n_q = sum(b[2] for b in bursts)
+    E_d = torch.from_numpy(E.reshape(-1)).to(dev)
+    ins_d = torch.ones(len(E), dtype=torch.int8, device=dev)
+    P_d = torch.from_numpy(WL.uniform_pairs(V, n_q, g_rng, distinct=False).reshape(-1)).to(dev)
+    out_d = torch.empty(n_q, dtype=torch.uint8, device=dev)
+    st, g = C.cupc_init(V, 1, None, None, stream)
+    C.check(st)
+
+    def run(sample_every=0):
+        lat, q = [], 0
+        for k, (i, n, m) in enumerate(bursts):
+            sample = sample_every and k % sample_every == sample_every - 1
+            if sample:
+                torch.cuda.synchronize()
+                t = time.perf_counter()
+            C.check(C.cupc_update_batch(g, E_d[2 * i:], ins_d[i:], n, stream))
+            C.check(C.cupc_query(g, P_d[2 * q:], m, out_d[q:], stream))
+            if sample:
+                torch.cuda.synchronize()
+                lat.append((time.perf_counter() - t) * 1e6)
+            q += m
+        return lat
+
+    run()  # warm-up pass
+    C.check(C.cupc_reset(g, stream))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    run()
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    C.check(C.cupc_reset(g, stream))
+    lat = run(sample_every=25)
+    C.cupc_destroy(g)
+    return {"workload": f"V=8192 ER(0.5) random-order inserts, first {len(E)} updates, query bursts of rho/9 "
+                        "pairs every rho ~ U[1000,2000] updates",
+            "updates_per_s": len(E) / dt, "queries_per_s": n_q / dt, "bursts": len(bursts),
+            "burst_latency_p50_us": statistics.median(lat), "burst_latency_p99_us": float(np.percentile(lat, 99)),
+            "paper_cupcake_k13_std_48core_epyc": {"updates_per_s": 1.79e6, "queries_per_s": 3.37e6}}
 
 
 def plain_stream_latency(torch, C, dev, stream):
