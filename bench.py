@@ -580,10 +580,11 @@ def paper_stream(torch, C, dev, stream, n_upd=1 << 21):
     (about the K13 density) in a seeded random order, inserted one burst of
     rho ~ U[1000, 2000] updates at a time, each followed by rho/9 uniform
     Connected pairs (10% of the operations are queries). The first n_upd
-    updates of the standard stream (insert all, then delete all) are run:
-    updates/s and queries/s over the whole prefix, and the latency of a
-    sampled burst's query (host submit -> answers ready, recovery
-    included)."""
+    updates of the standard stream (insert all, then delete all) are run,
+    with a full recovery per query burst and with incremental labels
+    (cupc_set_incremental): updates/s and queries/s over the whole prefix,
+    and the latency of a sampled burst (its update batch and its queries,
+    host submit -> answers ready)."""
     V, g_rng = 1 << 13, WL.rng(13)
     E = WL.er_edges(V, 0.5, 13)
     E = E[g_rng.permutation(len(E))][:n_upd]
@@ -616,21 +617,26 @@ def paper_stream(torch, C, dev, stream, n_upd=1 << 21):
             q += m
         return lat
 
-    run()  # warm-up pass
-    C.check(C.cupc_reset(g, stream))
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    run()
-    torch.cuda.synchronize()
-    dt = time.perf_counter() - t0
-    C.check(C.cupc_reset(g, stream))
-    lat = run(sample_every=25)
+    res = {"workload": f"V=8192 ER(0.5) random-order inserts, first {len(E)} updates, query bursts of rho/9 "
+                       "pairs every rho ~ U[1000,2000] updates", "bursts": len(bursts),
+           "paper_cupcake_k13_std_48core_epyc": {"updates_per_s": 1.79e6, "queries_per_s": 3.37e6}}
+    for mode, inc in (("recovery_per_burst", 0), ("incremental_labels", 1)):
+        C.check(C.cupc_set_incremental(g, inc, stream))
+        C.check(C.cupc_reset(g, stream))
+        run()  # warm-up pass
+        C.check(C.cupc_reset(g, stream))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        run()
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        C.check(C.cupc_reset(g, stream))
+        lat = run(sample_every=25)
+        res[mode] = {"updates_per_s": len(E) / dt, "queries_per_s": n_q / dt,
+                     "burst_latency_p50_us": statistics.median(lat),
+                     "burst_latency_p99_us": float(np.percentile(lat, 99))}
     C.cupc_destroy(g)
-    return {"workload": f"V=8192 ER(0.5) random-order inserts, first {len(E)} updates, query bursts of rho/9 "
-                        "pairs every rho ~ U[1000,2000] updates",
-            "updates_per_s": len(E) / dt, "queries_per_s": n_q / dt, "bursts": len(bursts),
-            "burst_latency_p50_us": statistics.median(lat), "burst_latency_p99_us": float(np.percentile(lat, 99)),
-            "paper_cupcake_k13_std_48core_epyc": {"updates_per_s": 1.79e6, "queries_per_s": 3.37e6}}
+    return res
 
 
 def plain_stream_latency(torch, C, dev, stream):

@@ -107,6 +107,19 @@ cupc_status cupc_reset(cupc_graph* g, cupc_stream stream);
 cupc_status cupc_update_batch(cupc_graph* g, const uint32_t* edges, const int8_t* ops, size_t n,
                               cupc_stream stream);
 
+/* Incremental labels (on != 0), off by default. After a complete recovery,
+ * each update batch keeps the component labels exact without sketch work as
+ * long as it only inserts edges, or deletes edges outside the recovered
+ * spanning forest while no insert has merged components since that
+ * recovery: a query then skips the Boruvka recovery. Any other batch (or a
+ * reset, an import, a host batch staged in several chunks) clears the
+ * labels and the next query recovers in full. This relies on the stream
+ * being valid (insert only absent edges, delete only present ones); with an
+ * invalid stream the sketches toggle while the labels merge, and answers can
+ * differ from a recovery's. cupc_spanning_forest always returns the forest
+ * of a full recovery of the current sketches. Stream-ordered on `stream`. */
+cupc_status cupc_set_incremental(cupc_graph* g, int on, cupc_stream stream);
+
 /* Answer m Connected(u,v) queries (Problem 2): out[i] = 1 iff pairs[2i] and
  * pairs[2i+1] are in the same recovered component. Runs Boruvka recovery
  * first if an update happened since the last one. pairs: 2m u32; out: m u8.

@@ -56,7 +56,7 @@ struct Layout {
   size_t sketch, keys, gc, cnt, cursor, rec, recw, items, part, stage_edges, stage_ops, stage_edges1, stage_ops1,
       label, parent, minv, rcnt, roff,
       perm, permb, pcount, final_, merged, best, best2, cand, forest, forest_sorted, acc, log_ids, log_live,
-      log_ncand, hlist, total;
+      log_ncand, hlist, ipar, total;
 };
 
 Layout layout(const Dims& d) {
@@ -102,6 +102,7 @@ Layout layout(const Dims& d) {
   l.log_live = take(d.L * 4);
   l.log_ncand = take(d.L * 4);
   l.hlist = take(kSmallHook * sizeof(ulonglong2));
+  l.ipar = take(V * 4);
   l.total = off;
   return l;
 }
@@ -127,10 +128,23 @@ cupc_status from_cuda(cudaError_t e) {
     if (e_ != cudaSuccess) return from_cuda(e_); \
   } while (0)
 
+// Incremental mode keeps the forest sorted after every recovery: a batch's
+// deletes look up the forest (k_incr). The recovery returns at once while
+// the labels are valid, and the sort while the forest is sorted.
 cupc_status recover_if_dirty(cupc_graph* g, cudaStream_t s) {
   if (!g->dirty) return CUPC_OK;
   CUPC_TRY(launch_recover(g, s));
+  if (g->inc) CUPC_TRY(launch_forest_sort(g, s));
   g->dirty = false;
+  return CUPC_OK;
+}
+
+// Updates invalidate the forest; in incremental mode a change the labels
+// cannot follow (a reset, imported sketches) clears them.
+cupc_status mark_updated(cupc_graph* g, cudaStream_t s, bool labels_kept) {
+  g->dirty = true;
+  g->forest_stale = true;
+  if (g->inc && !labels_kept) CUPC_TRY(cudaMemsetAsync(g->gc + GC_LABELS_VALID, 0, sizeof(uint32_t), s));
   return CUPC_OK;
 }
 
@@ -219,6 +233,7 @@ cupc_status cupc_init(uint32_t V, uint64_t seed, const cupc_params* params, void
   g->log_live = (uint32_t*)(b + l.log_live);
   g->log_ncand = (uint32_t*)(b + l.log_ncand);
   g->hlist = (ulonglong2*)(b + l.hlist);
+  g->ipar = (uint32_t*)(b + l.ipar);
   if (setup_update(g) != cudaSuccess || setup_recover(g) != cudaSuccess) {
     cudaGetLastError();
     return fail(CUPC_ECUDA);
@@ -229,6 +244,7 @@ cupc_status cupc_init(uint32_t V, uint64_t seed, const cupc_params* params, void
   }
   // the empty graph: every vertex its own component, recovery exact
   g->dirty = true;
+  g->forest_stale = true;
   *out = g;
   return CUPC_OK;
 }
@@ -237,8 +253,7 @@ cupc_status cupc_reset(cupc_graph* g, cupc_stream stream) {
   if (!g) return CUPC_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
   CUPC_TRY(cudaMemsetAsync(g->sketch, 0, (size_t)g->L * g->V * g->W * sizeof(ulonglong2), s));
-  g->dirty = true;
-  return CUPC_OK;
+  return mark_updated(g, s, false);
 }
 
 // The copy stream and slot events of host-input staging, made on first use.
@@ -270,6 +285,8 @@ cupc_status cupc_update_batch(cupc_graph* g, const uint32_t* edges, const int8_t
   if (dev_e && dev_o) {
     CUPC_TRY(launch_validate(g, edges, ops, n, s));
     for (size_t i = 0; i < n; i += B) CUPC_TRY(launch_update_chunk(g, edges + 2 * i, (n - i < B ? n - i : B), s));
+    if (g->inc) CUPC_TRY(launch_incremental(g, edges, ops, n, s));
+    return mark_updated(g, s, true);
   } else if (!dev_e && !dev_o && n <= B) {
     // host input, one chunk: copy on the graph's copy stream into the
     // staging slot not used last, so that the copy overlaps the kernels of
@@ -286,7 +303,9 @@ cupc_status cupc_update_batch(cupc_graph* g, const uint32_t* edges, const int8_t
     CUPC_TRY(cudaStreamWaitEvent(s, g->slot_ready[k], 0));
     CUPC_TRY(launch_validate(g, se, so, n, s));
     CUPC_TRY(launch_update_chunk(g, se, n, s));
+    if (g->inc) CUPC_TRY(launch_incremental(g, se, so, n, s));
     CUPC_TRY(mark_slot_free(g, k, s));
+    return mark_updated(g, s, true);
   } else {
     // a host input mixed with a device one, or several chunks: stage in
     // slot 0 on the caller's stream; a multi-chunk batch is validated in
@@ -315,9 +334,9 @@ cupc_status cupc_update_batch(cupc_graph* g, const uint32_t* edges, const int8_t
       }
     }
     CUPC_TRY(mark_slot_free(g, 0, s));
+    // staged chunk by chunk: the labels are not followed (cleared)
+    return mark_updated(g, s, false);
   }
-  g->dirty = true;
-  return CUPC_OK;
 }
 
 cupc_status cupc_query(cupc_graph* g, const uint32_t* pairs, size_t m, uint8_t* out, cupc_stream stream) {
@@ -369,8 +388,14 @@ cupc_status cupc_spanning_forest(cupc_graph* g, uint64_t* edge_ids_out, size_t c
                                  cupc_stream stream) {
   if (!g || !n_out) return CUPC_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
-  cupc_status st = recover_if_dirty(g, s);
-  if (st != CUPC_OK) return st;
+  if (g->inc && g->forest_stale) {  // labels may be incremental: the forest needs a recovery
+    CUPC_TRY(launch_recover(g, s, true));
+    g->dirty = false;
+  } else {
+    cupc_status st = recover_if_dirty(g, s);
+    if (st != CUPC_OK) return st;
+  }
+  g->forest_stale = false;
   CUPC_TRY(launch_forest_sort(g, s));
   uint32_t h[GC_SLOTS];
   CUPC_TRY(cudaMemcpyAsync(h, g->gc, sizeof(h), cudaMemcpyDeviceToHost, s));
@@ -413,7 +438,18 @@ cupc_status cupc_import_sketches(cupc_graph* g, const void* src, size_t bytes, c
   if (bytes != want) return CUPC_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
   CUPC_TRY(cudaMemcpyAsync(g->sketch, src, want, cudaMemcpyDefault, s));
+  const cupc_status st = mark_updated(g, s, false);
+  if (st != CUPC_OK) return st;
   CUPC_TRY(cudaStreamSynchronize(s));
+  return CUPC_OK;
+}
+
+cupc_status cupc_set_incremental(cupc_graph* g, int on, cupc_stream stream) {
+  if (!g) return CUPC_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  g->inc = on != 0;
+  // labels become incremental after the next complete recovery
+  CUPC_TRY(cudaMemsetAsync(g->gc + GC_LABELS_VALID, 0, sizeof(uint32_t), s));
   g->dirty = true;
   return CUPC_OK;
 }

@@ -86,6 +86,10 @@ enum : uint32_t {
   GC_NDIRECT = 18,   // direct-path records of the current chunk
   GC_NLIVE = 19,     // live components of the next recovery round
   GC_REC_DIRTY = 20, // a recovery gave up at a barrier: its scratch may be non-zero
+  GC_LABELS_VALID = 21,  // incremental mode: labels hold the current graph's components
+  GC_FOREST_SORTED = 22, // forest_sorted holds the last recovery's forest
+  GC_INC_MERGES = 23,    // incremental merges since the last recovery
+  GC_BATCH_DEL = 24,     // the current batch deletes an edge (incremental mode)
   GC_SLOTS = 32
 };
 
@@ -128,6 +132,8 @@ struct cupc_graph {
   size_t ws_bytes;
   bool owns_ws;
   bool dirty;
+  bool inc;           // incremental labels (cupc_set_incremental)
+  bool forest_stale;  // an update since the last full recovery
   int device, sms;
   int apply_threads, apply_smem, apply_grid;
   uint32_t item_records, apply_cps;  // tunables: records per work item, CTAs per SM (0 = max)
@@ -182,6 +188,7 @@ struct cupc_graph {
   uint32_t* log_live;   // L
   uint32_t* log_ncand;  // L
   ulonglong2* hlist;    // kSmallHook: crossing candidates of a hook step (recovery)
+  uint32_t* ipar;       // V: union-find over labels for incremental inserts
   cupc_status last_recovery;
   // profiling: (kernel class, start, stop, launches) per recorded launch group
   struct ProfRec {
@@ -237,7 +244,8 @@ inline uint32_t tune_bucket(size_t n) {
 }
 cudaError_t raise_apply_smem_limit(int bytes);
 cudaError_t setup_recover(cupc_graph* g);
-cudaError_t launch_recover(cupc_graph* g, cudaStream_t s);
+cudaError_t launch_recover(cupc_graph* g, cudaStream_t s, bool force = false);
 cudaError_t launch_query(cupc_graph* g, const uint32_t* pairs, size_t m, uint8_t* out, cudaStream_t s);
 cudaError_t launch_forest_sort(cupc_graph* g, cudaStream_t s);
+cudaError_t launch_incremental(cupc_graph* g, const uint32_t* edges, const int8_t* ops, size_t n, cudaStream_t s);
 }  // namespace cupc

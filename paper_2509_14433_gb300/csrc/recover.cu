@@ -42,6 +42,8 @@ struct RecArgs {
   ulonglong2* acc;
   uint32_t *log_live, *log_ncand;
   ulonglong2* hlist;  // kSmallHook: crossing candidates {edge, root_a << 32 | root_b} of a hook step
+  uint32_t* ipar;     // V: union-find of incremental inserts, identity after a recovery
+  uint32_t inc, force;  // incremental mode; run even if the labels are valid
   uint32_t* gc;
 };
 
@@ -350,6 +352,9 @@ __global__ void __launch_bounds__(kRecThreads, 2) k_recover(RecArgs a) {
 #define CUPC_GRID_SYNC() \
   if (!grid_barrier(gc, nb, epoch, &s_ok)) return
 
+  // incremental mode: the updates since the last recovery kept the labels
+  // exact (see k_incr), so there is nothing to recover
+  if (!a.force && ld_cg(&gc[GC_LABELS_VALID])) return;
   // after a recovery that gave up at a barrier, the reduce accumulators and
   // the last-arriver counters may hold partial sums: clear them first
   const bool dirty = ld_cg(&gc[GC_REC_DIRTY]) != 0;
@@ -363,11 +368,15 @@ __global__ void __launch_bounds__(kRecThreads, 2) k_recover(RecArgs a) {
     a.best0[w] = kNone;
     a.best1[w] = kNone;
     a.rcnt[w] = 0;
+    a.ipar[w] = w;
     if (dirty) a.pcount[w] = 0;
   }
   if (dirty)
     for (size_t i = gtid; i < (size_t)V * W; i += gstride) a.acc[i] = make_ulonglong2(0, 0);
   if (gtid == 0) {
+    gc[GC_LABELS_VALID] = 0;
+    gc[GC_FOREST_SORTED] = 0;
+    gc[GC_INC_MERGES] = 0;
     gc[GC_NFOREST] = 0;
     gc[GC_NFAIL] = 0;
     gc[GC_NFP] = 0;
@@ -763,6 +772,8 @@ __global__ void __launch_bounds__(kRecThreads, 2) k_recover(RecArgs a) {
     }
     CUPC_GRID_SYNC();
   }
+  // a complete recovery starts an incremental epoch
+  if (a.inc && gtid == 0) gc[GC_LABELS_VALID] = ld_cg(&gc[GC_COMPLETE]);
 #undef CUPC_GRID_SYNC
 }
 
@@ -791,7 +802,7 @@ cudaError_t setup_recover(cupc_graph* g) {
   return cudaSuccess;
 }
 
-cudaError_t launch_recover(cupc_graph* g, cudaStream_t s) {
+cudaError_t launch_recover(cupc_graph* g, cudaStream_t s, bool force) {
   RecArgs a;
   a.sketch = g->sketch;
   a.keys = g->keys;
@@ -819,6 +830,9 @@ cudaError_t launch_recover(cupc_graph* g, cudaStream_t s) {
   a.log_live = g->log_live;
   a.log_ncand = g->log_ncand;
   a.hlist = g->hlist;
+  a.ipar = g->ipar;
+  a.inc = g->inc ? 1u : 0u;
+  a.force = force ? 1u : 0u;
   a.gc = g->gc;
   cudaError_t e = cudaMemsetAsync(g->gc + GC_BAR_COUNT, 0, sizeof(uint32_t), s);
   if (e != cudaSuccess) return e;
@@ -887,6 +901,7 @@ constexpr uint32_t kSortChunk = 1024;
 
 __global__ void __launch_bounds__(512) k_sort_chunks(uint64_t* ids, const uint32_t* gc) {
   __shared__ uint64_t s[kSortChunk];
+  if (ld_cg(&gc[GC_FOREST_SORTED])) return;  // done since the last recovery
   const uint32_t n = ld_cg(&gc[GC_NFOREST]);
   const uint32_t base = blockIdx.x * kSortChunk;
   if (base >= n) return;
@@ -912,6 +927,7 @@ __global__ void __launch_bounds__(512) k_sort_chunks(uint64_t* ids, const uint32
 }
 
 __global__ void k_merge_rank(const uint64_t* __restrict__ ids, uint64_t* __restrict__ out, const uint32_t* gc) {
+  if (ld_cg(&gc[GC_FOREST_SORTED])) return;
   const uint32_t n = ld_cg(&gc[GC_NFOREST]);
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -933,11 +949,14 @@ __global__ void k_merge_rank(const uint64_t* __restrict__ ids, uint64_t* __restr
   out[rank] = x;
 }
 
+__global__ void k_mark_sorted(uint32_t* gc) { gc[GC_FOREST_SORTED] = 1; }
+
 cudaError_t launch_forest_sort(cupc_graph* g, cudaStream_t s) {
   uint32_t nch = (g->V + kSortChunk - 1) / kSortChunk;
-  ProfScope ps(g, s, PC_SORT, 2);
+  ProfScope ps(g, s, PC_SORT, 3);
   k_sort_chunks<<<nch, 512, 0, s>>>(g->forest, g->gc);
   k_merge_rank<<<(g->V + 255) / 256, 256, 0, s>>>(g->forest, g->forest_sorted, g->gc);
+  k_mark_sorted<<<1, 1, 0, s>>>(g->gc);
   return cudaGetLastError();
 }
 

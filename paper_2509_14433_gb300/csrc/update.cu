@@ -124,6 +124,95 @@ __global__ void __launch_bounds__(1024) k_scatter_priv(const uint32_t* __restric
   }
 }
 
+// ---- incremental labels (cupc_set_incremental). After a complete
+// recovery the labels are the components of the graph; with a valid stream
+// (inserts of absent edges, deletes of present ones) an insert can only
+// merge two components, and deleting an edge outside the recovered spanning
+// forest cannot split one. So a batch keeps the labels exact by merging the
+// endpoint labels of its inserts (union-find over labels, the larger root
+// under the smaller, so a root is its component's minimum vertex id, the
+// label a recovery gives); a batch that deletes a forest edge, or deletes
+// anything once an insert has merged components since the recovery, clears
+// GC_LABELS_VALID and the next query recovers in full.
+__device__ __forceinline__ uint32_t inc_find(uint32_t* par, uint32_t x, uint32_t V) {
+  for (uint32_t k = 0; k < V; k++) {  // a path is shorter than V
+    const uint32_t y = ld_cg(&par[x]);
+    if (y == x) break;
+    const uint32_t z = ld_cg(&par[y]);
+    if (z != y) par[x] = z;  // halving: only ever to an ancestor
+    x = y;
+  }
+  return x;
+}
+
+__global__ void k_incr(const uint32_t* __restrict__ edges, const int8_t* __restrict__ ops, size_t n, uint32_t V,
+                       const uint32_t* __restrict__ label, uint32_t* ipar, const uint64_t* __restrict__ forest_sorted,
+                       uint32_t* gc) {
+  if ((ld_cg(&gc[GC_ERR]) & kErrInval) || !ld_cg(&gc[GC_LABELS_VALID])) return;
+  const uint32_t nf = ld_cg(&gc[GC_NFOREST]);
+  bool del = false, merged = false, cut = false;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const uint32_t u = edges[2 * i], v = edges[2 * i + 1];
+    if (ops[i] < 0) {
+      del = true;
+      const uint64_t id = (uint64_t)min(u, v) * V + max(u, v);
+      uint32_t lo = 0, hi = nf;  // first forest id >= id
+      while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (forest_sorted[mid] < id)
+          lo = mid + 1;
+        else
+          hi = mid;
+      }
+      if (lo < nf && forest_sorted[lo] == id) cut = true;
+    } else {
+      uint32_t a = label[u], b = label[v];
+      for (uint32_t k = 0; k < (1u << 20); k++) {  // bounded retries; giving up clears the labels
+        a = inc_find(ipar, a, V);
+        b = inc_find(ipar, b, V);
+        if (a == b) break;
+        if (a > b) {
+          const uint32_t t = a;
+          a = b;
+          b = t;
+        }
+        if (atomicCAS(&ipar[b], b, a) == b) {
+          merged = true;
+          break;
+        }
+        if (k + 1 == (1u << 20)) cut = true;
+      }
+    }
+  }
+  if (__any_sync(0xffffffffu, cut) && (threadIdx.x & 31) == 0) gc[GC_LABELS_VALID] = 0;
+  if (__any_sync(0xffffffffu, del) && (threadIdx.x & 31) == 0) gc[GC_BATCH_DEL] = 1;
+  if (__any_sync(0xffffffffu, merged) && (threadIdx.x & 31) == 0) gc[GC_INC_MERGES] = 1;
+}
+
+// Labels after the merges: every vertex takes its label's root. A batch that
+// both deletes and follows a merge clears the labels instead.
+__global__ void k_incr_finish(uint32_t* label, uint32_t* ipar, uint32_t V, uint32_t* gc) {
+  if (!ld_cg(&gc[GC_LABELS_VALID])) return;
+  if (ld_cg(&gc[GC_BATCH_DEL]) && ld_cg(&gc[GC_INC_MERGES])) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) gc[GC_LABELS_VALID] = 0;
+    return;
+  }
+  if (!ld_cg(&gc[GC_INC_MERGES])) return;  // nothing merged since the recovery
+  for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < V; w += gridDim.x * blockDim.x)
+    label[w] = inc_find(ipar, label[w], V);
+}
+
+cudaError_t launch_incremental(cupc_graph* g, const uint32_t* edges, const int8_t* ops, size_t n, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(g->gc + GC_BATCH_DEL, 0, sizeof(uint32_t), s);
+  if (e != cudaSuccess) return e;
+  const int grid = (int)std::min<size_t>((n + 255) / 256, (size_t)g->sms * 8);
+  k_incr<<<grid, 256, 0, s>>>(edges, ops, n, g->V, g->label, g->ipar, g->forest_sorted, g->gc);
+  k_incr_finish<<<(int)std::min<size_t>((g->V + 255) / 256, (size_t)g->sms * 4), 256, 0, s>>>(g->label, g->ipar,
+                                                                                                g->V, g->gc);
+  return cudaGetLastError();
+}
+
 // Work plan of one chunk over many CTAs, in two launches that never wait on
 // one another. The vertices are cut into slices of 256 * vpt; slice b is
 // planned by CTA b. Kinds of vertices and the layout of records and items

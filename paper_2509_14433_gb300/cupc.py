@@ -46,6 +46,7 @@ _SIGS = {
     "cupc_get_params": (ctypes.c_int, [_P, _P]),
     "cupc_set_tuning": (ctypes.c_int, [_P, _u32, _u32, _u32]),
     "cupc_set_tuning_bucket": (ctypes.c_int, [_P, _u32, _u32, _u32, _u32]),
+    "cupc_set_incremental": (ctypes.c_int, [_P, ctypes.c_int, _P]),
     "cupc_update_batches": (ctypes.c_int, [_P, _P, _P, _P, _sz, _P]),
     "cupc_batcher_create": (ctypes.c_int, [_u32, ctypes.c_int, _P]),
     "cupc_batcher_update": (ctypes.c_int, [_P, _P, _P, _P, _P, _u32, _P]),
@@ -253,6 +254,10 @@ def cupc_set_tuning(g, item_records: int, smem_rows: int, ctas_per_sm: int) -> i
 
 def cupc_set_tuning_bucket(g, bucket: int, item_records: int, smem_rows: int, ctas_per_sm: int) -> int:
     return _lib.cupc_set_tuning_bucket(g, bucket, item_records, smem_rows, ctas_per_sm)
+
+
+def cupc_set_incremental(g, on: int, stream=None) -> int:
+    return _lib.cupc_set_incremental(g, on, stream_handle(stream))
 
 
 def cupc_get_tuning(g, out4) -> int:

@@ -1,0 +1,99 @@
+"""Incremental labels (cupc_set_incremental): on a valid stream, every
+Connected answer equals the oracle's (a full recovery from the sketches),
+queries after insert-only batches skip the recovery, a deleted forest edge
+brings it back, and the spanning forest is always a full recovery's."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2509_14433_gb300 import workloads as WL
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+
+
+def _dev(*a, **k):
+    from tests._dev import Dev
+    return Dev(*a, **k)
+
+
+def _absent_pairs(V, k, present, g):
+    out = []
+    while len(out) < k:
+        u, v = (int(x) for x in g.integers(0, V, 2))
+        if u == v:
+            continue
+        a, b = min(u, v), max(u, v)
+        if a * V + b not in present and (a, b) not in out:
+            out.append((a, b))
+    return np.array(out, np.uint32)
+
+
+def test_incremental_labels_match_full_recovery():
+    from paper_2509_14433_gb300 import cupc as C
+    from tests.test_gpu_parity import assert_same_recovery
+    V, seed = 1500, 31
+    g = WL.rng(seed)
+    dev, ref = _dev(V, seed), O.Graph(V, seed)
+    assert C.cupc_set_incremental(dev.h, 1, None) == 0
+    E0 = WL.er_edges(V, 0.0008, seed)  # sparse: many components to merge
+    present = set(int(a) * V + int(b) for a, b in E0)
+    assert dev.update(E0) == 0 and ref.update(E0) == O.OK
+    queries = 0
+    plan = ["ins"] * 12 + ["del"] * 4 + ["ins"] * 6 + ["mix"] * 3 + ["ins"] * 4
+    for kind in plan:
+        if kind in ("ins", "mix"):
+            E = _absent_pairs(V, int(g.integers(1, 200)), present, g)
+            ops = np.ones(len(E), np.int8)
+            present.update(int(a) * V + int(b) for a, b in E)
+        if kind in ("del", "mix"):
+            ids = np.array(sorted(present), np.int64)
+            pick = ids[g.choice(len(ids), min(len(ids), int(g.integers(1, 60))), replace=False)]
+            D = np.stack([pick // V, pick % V], 1).astype(np.uint32)
+            present.difference_update(int(x) for x in pick)
+            if kind == "mix":  # deletes first: a valid order
+                E, ops = np.concatenate([D, E]), np.concatenate([-np.ones(len(D), np.int8), ops])
+            else:
+                E, ops = D, -np.ones(len(D), np.int8)
+        assert dev.update(E, ops) == 0 and ref.update(E, ops) == O.OK
+        pairs = WL.uniform_pairs(V, 500, g, distinct=False)
+        s1, a1 = dev.query(pairs)
+        s2, a2 = ref.query(pairs)
+        assert s1 == s2 == 0 and np.array_equal(a1, a2), kind
+        queries += 1
+    st = dev.stats()
+    # the first query recovers; insert-only batches after it do not
+    assert st["recoveries"] < queries - 10, st
+    assert np.array_equal(dev.labels(), ref.labels())
+    # the forest is a full recovery's, bit-exact with the oracle's
+    assert_same_recovery(dev, ref)
+    assert dev.stats()["recoveries"] == st["recoveries"] + 1
+
+
+def test_incremental_off_by_default_and_switchable():
+    from paper_2509_14433_gb300 import cupc as C
+    V = 400
+    dev, ref = _dev(V, 5), O.Graph(V, 5)
+    E = WL.er_edges(V, 0.01, 5)
+    assert dev.update(E) == 0 and ref.update(E) == O.OK
+    p = WL.uniform_pairs(V, 200, WL.rng(5), distinct=False)
+    present = set(int(a) * V + int(b) for a, b in E)
+    e = np.array([next((0, v) for v in range(1, V) if v not in present)], np.uint32)  # an absent edge
+    for on in (0, 1, 0):
+        assert C.cupc_set_incremental(dev.h, on, None) == 0
+        n0 = dev.stats()["recoveries"]
+        for k in range(4):  # insert, delete, insert, delete: a valid stream
+            s1, a1 = dev.query(p)
+            assert np.array_equal(a1, ref.query(p)[1])
+            op = np.array([1 if k % 2 == 0 else -1], np.int8)
+            assert dev.update(e, op) == 0 and ref.update(e, op) == O.OK
+        if not on:  # off: every query after an update recovers
+            assert dev.stats()["recoveries"] == n0 + 4
+    assert C.cupc_set_incremental(None, 1, None) == C.CUPC_EINVAL
