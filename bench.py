@@ -320,6 +320,7 @@ def run_gpu(args):
 
     # ---- plain V=1024 toggle stream: updates/s and query latency
     plain = plain_stream_latency(torch, C, dev, stream)
+    plain.update(plain_stream_latency(torch, C, dev, stream, inc=1))
     pstream = None if args.no_batching else paper_stream(torch, C, dev, stream)
     batching = None if args.no_batching else batching_compare(torch, C, dev, stream)
     serving = None if args.no_serving else serving_compare(torch, C, dev)
@@ -639,14 +640,17 @@ def paper_stream(torch, C, dev, stream, n_upd=1 << 21):
     return res
 
 
-def plain_stream_latency(torch, C, dev, stream):
+def plain_stream_latency(torch, C, dev, stream, inc=0):
     """V=1024 ER(0.5) start graph + 200k toggles, a 1k-pair Connected batch
     every 10k updates: updates/s over the toggles, query latency p50/p99
-    (host submit -> answers ready, recovery included)."""
+    (host submit -> answers ready, recovery included). inc: incremental
+    labels (the stream is valid: a toggle inserts an absent edge or deletes
+    a present one)."""
     V = 1024
     steps = WL.plain_stream(V=V, seed=1)
     st, g = C.cupc_init(V, 1, None, None, stream)
     C.check(st)
+    C.check(C.cupc_set_incremental(g, inc, stream))
     dsteps = []
     for s in steps:
         if s[0] == "update":
@@ -675,8 +679,9 @@ def plain_stream_latency(torch, C, dev, stream):
             else:
                 lat.append(dt * 1e6)
     C.cupc_destroy(g)
-    return {"plain_v1024_p50": statistics.median(lat), "plain_v1024_p99": float(np.percentile(lat, 99)),
-            "plain_v1024_toggle_updates_per_s": n_upd / upd_t, "plain_v1024_queries": len(lat)}
+    sfx = "_incremental" if inc else ""
+    return {f"plain_v1024{sfx}_p50": statistics.median(lat), f"plain_v1024{sfx}_p99": float(np.percentile(lat, 99)),
+            f"plain_v1024{sfx}_toggle_updates_per_s": n_upd / upd_t, f"plain_v1024{sfx}_queries": len(lat)}
 
 
 def batch_latency_sweep(torch, C, g, D_d, ins_d, del_d, p_d, q_out, stream):

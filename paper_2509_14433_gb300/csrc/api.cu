@@ -56,7 +56,7 @@ struct Layout {
   size_t sketch, keys, gc, cnt, cursor, rec, recw, items, part, stage_edges, stage_ops, stage_edges1, stage_ops1,
       label, parent, minv, rcnt, roff,
       perm, permb, pcount, final_, merged, best, best2, cand, forest, forest_sorted, acc, log_ids, log_live,
-      log_ncand, hlist, ipar, total;
+      log_ncand, hlist, ipar, fdead, total;
 };
 
 Layout layout(const Dims& d) {
@@ -103,6 +103,7 @@ Layout layout(const Dims& d) {
   l.log_ncand = take(d.L * 4);
   l.hlist = take(kSmallHook * sizeof(ulonglong2));
   l.ipar = take(V * 4);
+  l.fdead = take(V);
   l.total = off;
   return l;
 }
@@ -234,6 +235,7 @@ cupc_status cupc_init(uint32_t V, uint64_t seed, const cupc_params* params, void
   g->log_ncand = (uint32_t*)(b + l.log_ncand);
   g->hlist = (ulonglong2*)(b + l.hlist);
   g->ipar = (uint32_t*)(b + l.ipar);
+  g->fdead = (uint8_t*)(b + l.fdead);
   if (setup_update(g) != cudaSuccess || setup_recover(g) != cudaSuccess) {
     cudaGetLastError();
     return fail(CUPC_ECUDA);

@@ -90,6 +90,8 @@ enum : uint32_t {
   GC_FOREST_SORTED = 22, // forest_sorted holds the last recovery's forest
   GC_INC_MERGES = 23,    // incremental merges since the last recovery
   GC_BATCH_DEL = 24,     // the current batch deletes an edge (incremental mode)
+  GC_WARM = 25,          // incremental mode: forest edges were deleted, no merges: warm-start recovery
+  GC_NSORTED = 26,       // length of forest_sorted
   GC_SLOTS = 32
 };
 
@@ -189,6 +191,7 @@ struct cupc_graph {
   uint32_t* log_ncand;  // L
   ulonglong2* hlist;    // kSmallHook: crossing candidates of a hook step (recovery)
   uint32_t* ipar;       // V: union-find over labels for incremental inserts
+  uint8_t* fdead;       // V: forest_sorted[i] was deleted since the last recovery
   cupc_status last_recovery;
   // profiling: (kernel class, start, stop, launches) per recorded launch group
   struct ProfRec {

@@ -43,6 +43,8 @@ struct RecArgs {
   uint32_t *log_live, *log_ncand;
   ulonglong2* hlist;  // kSmallHook: crossing candidates {edge, root_a << 32 | root_b} of a hook step
   uint32_t* ipar;     // V: union-find of incremental inserts, identity after a recovery
+  const uint64_t* forest_sorted;
+  uint8_t* fdead;     // V: forest_sorted[i] deleted since the last recovery
   uint32_t inc, force;  // incremental mode; run even if the labels are valid
   uint32_t* gc;
 };
@@ -132,7 +134,8 @@ __device__ __forceinline__ uint32_t warp_sample(const ulonglong2 (&acc)[kWarpBuc
 // its candidate (stored with both endpoint labels) and is logged; GOOD with
 // an edge inside K is a checksum false positive. Counters are aggregated per
 // warp. Every lane of the warp must call this.
-__device__ __forceinline__ void book_samples(const RecArgs& a, uint32_t r, uint32_t K, uint32_t res, uint64_t e) {
+__device__ __forceinline__ void book_samples(const RecArgs& a, uint32_t r, bool multi, uint32_t K, uint32_t res,
+                                             uint64_t e) {
   const uint32_t lane = threadIdx.x & 31;
   const bool have = K != kNoneU32;
   bool cand = false;
@@ -141,7 +144,7 @@ __device__ __forceinline__ void book_samples(const RecArgs& a, uint32_t r, uint3
       a.final_[K] = 1;
     } else if (res == 1) {
       const uint32_t u = (uint32_t)(e / a.V), v = (uint32_t)(e % a.V);
-      const uint32_t lu = r ? ld_cg(&a.label[u]) : u, lv = r ? ld_cg(&a.label[v]) : v;
+      const uint32_t lu = multi ? ld_cg(&a.label[u]) : u, lv = multi ? ld_cg(&a.label[v]) : v;
       if ((lu == K) != (lv == K)) {
         cand = true;
         a.cand[K] = make_ulonglong2(e, ((uint64_t)lu << 32) | lv);
@@ -353,8 +356,13 @@ __global__ void __launch_bounds__(kRecThreads, 2) k_recover(RecArgs a) {
   if (!grid_barrier(gc, nb, epoch, &s_ok)) return
 
   // incremental mode: the updates since the last recovery kept the labels
-  // exact (see k_incr), so there is nothing to recover
-  if (!a.force && ld_cg(&gc[GC_LABELS_VALID])) return;
+  // exact (see k_incr), so there is nothing to recover; or they deleted
+  // forest edges and merged nothing: then the components are unions of the
+  // fragments of the remaining forest, and Boruvka starts from those
+  // (warm start) instead of from single vertices
+  const bool valid = ld_cg(&gc[GC_LABELS_VALID]) != 0, warm = !a.force && valid && ld_cg(&gc[GC_WARM]) != 0;
+  if (!a.force && valid && !warm) return;
+  const uint32_t nsorted = warm ? ld_cg(&gc[GC_NSORTED]) : 0;
   // after a recovery that gave up at a barrier, the reduce accumulators and
   // the last-arriver counters may hold partial sums: clear them first
   const bool dirty = ld_cg(&gc[GC_REC_DIRTY]) != 0;
@@ -369,6 +377,7 @@ __global__ void __launch_bounds__(kRecThreads, 2) k_recover(RecArgs a) {
     a.best1[w] = kNone;
     a.rcnt[w] = 0;
     a.ipar[w] = w;
+    if (!warm) a.fdead[w] = 0;  // a warm start reads them first
     if (dirty) a.pcount[w] = 0;
   }
   if (dirty)
@@ -377,6 +386,8 @@ __global__ void __launch_bounds__(kRecThreads, 2) k_recover(RecArgs a) {
     gc[GC_LABELS_VALID] = 0;
     gc[GC_FOREST_SORTED] = 0;
     gc[GC_INC_MERGES] = 0;
+    gc[GC_WARM] = 0;
+    gc[GC_NLIVE] = 0;
     gc[GC_NFOREST] = 0;
     gc[GC_NFAIL] = 0;
     gc[GC_NFP] = 0;
@@ -396,15 +407,61 @@ __global__ void __launch_bounds__(kRecThreads, 2) k_recover(RecArgs a) {
   }
   CUPC_GRID_SYNC();
   if (dirty && gtid == 0) gc[GC_REC_DIRTY] = 0;  // every CTA has read it
+  if (warm) {
+    // fragments: union the endpoints of the forest edges still present (the
+    // larger root under the smaller), which also start the new forest
+    for (uint32_t base = gwarp * 32; base < nsorted; base += nwarps * 32) {
+      const uint32_t i = base + lane;
+      const bool keep = i < nsorted && !a.fdead[i];
+      uint64_t e = 0;
+      if (keep) {
+        e = a.forest_sorted[i];
+        uint32_t x = (uint32_t)(e / V), y = (uint32_t)(e % V);
+        for (uint32_t k = 0; k < V; k++) {  // bounded: each failed CAS is another thread's progress
+          x = find_root(a.parent, x, V);
+          y = find_root(a.parent, y, V);
+          if (x == y) break;
+          if (x > y) {
+            const uint32_t t = x;
+            x = y;
+            y = t;
+          }
+          if (atomicCAS(&a.parent[y], y, x) == y) break;
+        }
+      }
+      const uint32_t m = __ballot_sync(0xffffffffu, keep);
+      uint32_t at = 0;
+      if (lane == 0 && m) at = atomicAdd(&gc[GC_NFOREST], (uint32_t)__popc(m));
+      at = __shfl_sync(0xffffffffu, at, 0);
+      if (keep) a.forest[at + __popc(m & ((1u << lane) - 1))] = e;
+    }
+    CUPC_GRID_SYNC();
+    for (uint32_t w = gtid; w < V; w += gstride) a.label[w] = find_root(a.parent, w, V);  // the minimum id
+    CUPC_GRID_SYNC();
+    // fragments are the live components of the first round: count members
+    for (uint32_t base = gwarp * 32; base < V; base += nwarps * 32) {
+      const uint32_t w = base + lane;
+      uint32_t lab = 0;
+      if (w < V) {
+        lab = ld_cg(&a.label[w]);
+        a.parent[w] = w;
+        a.fdead[w] = 0;
+      }
+      const uint32_t m_first = __ballot_sync(0xffffffffu, warp_grab(a.rcnt, lab, w < V) == 0 && w < V);
+      if (lane == 0 && m_first) atomicAdd(&gc[GC_NLIVE], (uint32_t)__popc(m_first));
+    }
+    CUPC_GRID_SYNC();
+  }
 
   for (uint32_t r = 0; r < a.L; r++) {
     const uint64_t kchk = a.keys[r * (a.C + 1) + a.C];
+    const bool multi = r > 0 || warm;  // components may have several members
     // One live component left: every other component is final, and a final
     // component's merged sketch is zero (its cut is empty); the XOR of all
     // vertex sketches of a layer is zero (each edge enters both endpoints),
     // so the live one's merged sketch is zero too and it samples ZERO. Log
     // the round as sampled (one live component, no candidate) and stop.
-    if (r > 0 && ld_cg(&gc[GC_NLIVE]) == 1) {
+    if (multi && ld_cg(&gc[GC_NLIVE]) == 1) {
       if (gtid == 0) {
         a.log_live[r] = 1;
         gc[GC_ROUNDS] = r + 1;
@@ -416,7 +473,7 @@ __global__ void __launch_bounds__(kRecThreads, 2) k_recover(RecArgs a) {
     // round r-1 counted them; give each component a segment (warp-aggregated
     // atomics), then scatter
     uint32_t nmem = V;
-    if (r > 0) {
+    if (multi) {
       for (uint32_t base = blockIdx.x * blockDim.x; base < V; base += gstride) {
         const uint32_t K = base + tid;
         const uint32_t c = K < V ? ld_cg(&a.rcnt[K]) : 0;
@@ -462,7 +519,7 @@ __global__ void __launch_bounds__(kRecThreads, 2) k_recover(RecArgs a) {
     // ---- reduce + sample, one warp per span of members (round 0: one
     // vertex per span, every vertex is its own component). A component over
     // several spans is XORed into acc[K]; the last span to finish samples it.
-    if (r > 0) {
+    if (multi) {
       // big components (more than kRecSpan members): CTA tiles of up to
       // kRecTile members, thread t XORs bucket t of every member (8 rows in
       // flight);
@@ -546,7 +603,7 @@ __global__ void __launch_bounds__(kRecThreads, 2) k_recover(RecArgs a) {
           if (mine) {
             uint64_t e = 0;
             const uint32_t res = warp_sample(acc, W, V, kchk, e);
-            book_samples(a, r, lane == 0 ? K : kNoneU32, res, e);
+            book_samples(a, r, multi, lane == 0 ? K : kNoneU32, res, e);
           }
         }
         __syncthreads();
@@ -554,18 +611,18 @@ __global__ void __launch_bounds__(kRecThreads, 2) k_recover(RecArgs a) {
     }
 
     // small components (and every vertex in round 0): one warp per span
-    const uint32_t span = r == 0 ? 1u : kRecSpan;
+    const uint32_t span = multi ? kRecSpan : 1u;
     const uint32_t nspans = (nmem + span - 1) / span;
     uint32_t st_k = kNoneU32, st_res = 0, nst = 0;  // this lane's stashed sample
     uint64_t st_e = 0;
     for (uint32_t sp = gwarp; sp < nspans; sp += nwarps) {
       const uint32_t i0 = sp * span, cnt = min(span, nmem - i0);
-      if (r == 0 && sp + nwarps < nspans && lane * 8 < W)  // round 0: bring this warp's next row to L2
+      if (!multi && sp + nwarps < nspans && lane * 8 < W)  // round 0: bring this warp's next row to L2
         asm volatile("prefetch.global.L2 [%0];" ::"l"(a.sketch + (size_t)(sp + nwarps) * W + lane * 8));
       uint32_t mw = 0, mk = kNoneU32;
       if (lane < cnt) {
-        mw = r > 0 ? ld_cg(&a.perm[i0 + lane]) : i0 + lane;
-        mk = r > 0 ? ld_cg(&a.label[mw]) : mw;
+        mw = multi ? ld_cg(&a.perm[i0 + lane]) : i0 + lane;
+        mk = multi ? ld_cg(&a.label[mw]) : mw;
       }
       uint32_t i = 0;
       while (i < cnt) {
@@ -580,7 +637,7 @@ __global__ void __launch_bounds__(kRecThreads, 2) k_recover(RecArgs a) {
           warp_xor_row(acc, a.sketch + ((size_t)r * V + w) * W, W, lane);
         }
         uint32_t nsp = 1;
-        if (r > 0) {
+        if (multi) {
           const uint32_t s0 = ld_cg(&a.roff[K]), s1 = ld_cg(&a.rcnt[K]);
           nsp = (s1 - 1) / span - s0 / span + 1;
         }
@@ -622,7 +679,7 @@ __global__ void __launch_bounds__(kRecThreads, 2) k_recover(RecArgs a) {
             st_e = e;
           }
           if (++nst == 32) {  // book 32 samples at once, one per lane
-            book_samples(a, r, st_k, st_res, st_e);
+            book_samples(a, r, multi, st_k, st_res, st_e);
             st_k = kNoneU32;
             nst = 0;
           }
@@ -630,7 +687,7 @@ __global__ void __launch_bounds__(kRecThreads, 2) k_recover(RecArgs a) {
         i = j;
       }
     }
-    if (nst) book_samples(a, r, st_k, st_res, st_e);
+    if (nst) book_samples(a, r, multi, st_k, st_res, st_e);
     CUPC_GRID_SYNC();
     if (gtid == 0) gc[GC_ROUNDS] = r + 1;
     if (ld_cg(&gc[GC_NZ]) == 0) {
@@ -831,6 +888,8 @@ cudaError_t launch_recover(cupc_graph* g, cudaStream_t s, bool force) {
   a.log_ncand = g->log_ncand;
   a.hlist = g->hlist;
   a.ipar = g->ipar;
+  a.forest_sorted = g->forest_sorted;
+  a.fdead = g->fdead;
   a.inc = g->inc ? 1u : 0u;
   a.force = force ? 1u : 0u;
   a.gc = g->gc;
@@ -949,7 +1008,11 @@ __global__ void k_merge_rank(const uint64_t* __restrict__ ids, uint64_t* __restr
   out[rank] = x;
 }
 
-__global__ void k_mark_sorted(uint32_t* gc) { gc[GC_FOREST_SORTED] = 1; }
+__global__ void k_mark_sorted(uint32_t* gc) {
+  if (gc[GC_FOREST_SORTED]) return;
+  gc[GC_NSORTED] = gc[GC_NFOREST];
+  gc[GC_FOREST_SORTED] = 1;
+}
 
 cudaError_t launch_forest_sort(cupc_graph* g, cudaStream_t s) {
   uint32_t nch = (g->V + kSortChunk - 1) / kSortChunk;

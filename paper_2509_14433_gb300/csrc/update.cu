@@ -131,8 +131,10 @@ __global__ void __launch_bounds__(1024) k_scatter_priv(const uint32_t* __restric
 // forest cannot split one. So a batch keeps the labels exact by merging the
 // endpoint labels of its inserts (union-find over labels, the larger root
 // under the smaller, so a root is its component's minimum vertex id, the
-// label a recovery gives); a batch that deletes a forest edge, or deletes
-// anything once an insert has merged components since the recovery, clears
+// label a recovery gives). A deleted forest edge is marked (fdead) and sets
+// GC_WARM: the next recovery starts from the fragments of the remaining
+// forest. A batch that deletes anything once an insert has merged components
+// since the recovery, or merges after forest edges were deleted, clears
 // GC_LABELS_VALID and the next query recovers in full.
 __device__ __forceinline__ uint32_t inc_find(uint32_t* par, uint32_t x, uint32_t V) {
   for (uint32_t k = 0; k < V; k++) {  // a path is shorter than V
@@ -147,10 +149,10 @@ __device__ __forceinline__ uint32_t inc_find(uint32_t* par, uint32_t x, uint32_t
 
 __global__ void k_incr(const uint32_t* __restrict__ edges, const int8_t* __restrict__ ops, size_t n, uint32_t V,
                        const uint32_t* __restrict__ label, uint32_t* ipar, const uint64_t* __restrict__ forest_sorted,
-                       uint32_t* gc) {
+                       uint8_t* fdead, uint32_t* gc) {
   if ((ld_cg(&gc[GC_ERR]) & kErrInval) || !ld_cg(&gc[GC_LABELS_VALID])) return;
-  const uint32_t nf = ld_cg(&gc[GC_NFOREST]);
-  bool del = false, merged = false, cut = false;
+  const uint32_t nf = ld_cg(&gc[GC_NSORTED]);
+  bool del = false, merged = false, cut = false, warm = false;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
     const uint32_t u = edges[2 * i], v = edges[2 * i + 1];
     if (ops[i] < 0) {
@@ -164,7 +166,10 @@ __global__ void k_incr(const uint32_t* __restrict__ edges, const int8_t* __restr
         else
           hi = mid;
       }
-      if (lo < nf && forest_sorted[lo] == id) cut = true;
+      if (lo < nf && forest_sorted[lo] == id) {
+        fdead[lo] = 1;
+        warm = true;
+      }
     } else {
       uint32_t a = label[u], b = label[v];
       for (uint32_t k = 0; k < (1u << 20); k++) {  // bounded retries; giving up clears the labels
@@ -187,13 +192,15 @@ __global__ void k_incr(const uint32_t* __restrict__ edges, const int8_t* __restr
   if (__any_sync(0xffffffffu, cut) && (threadIdx.x & 31) == 0) gc[GC_LABELS_VALID] = 0;
   if (__any_sync(0xffffffffu, del) && (threadIdx.x & 31) == 0) gc[GC_BATCH_DEL] = 1;
   if (__any_sync(0xffffffffu, merged) && (threadIdx.x & 31) == 0) gc[GC_INC_MERGES] = 1;
+  if (__any_sync(0xffffffffu, warm) && (threadIdx.x & 31) == 0) gc[GC_WARM] = 1;
 }
 
-// Labels after the merges: every vertex takes its label's root. A batch that
-// both deletes and follows a merge clears the labels instead.
+// Labels after the merges: every vertex takes its label's root. Merges that
+// meet deletes (this batch's, or deleted forest edges awaiting a warm start)
+// clear the labels instead.
 __global__ void k_incr_finish(uint32_t* label, uint32_t* ipar, uint32_t V, uint32_t* gc) {
   if (!ld_cg(&gc[GC_LABELS_VALID])) return;
-  if (ld_cg(&gc[GC_BATCH_DEL]) && ld_cg(&gc[GC_INC_MERGES])) {
+  if (ld_cg(&gc[GC_INC_MERGES]) && (ld_cg(&gc[GC_BATCH_DEL]) || ld_cg(&gc[GC_WARM]))) {
     if (blockIdx.x == 0 && threadIdx.x == 0) gc[GC_LABELS_VALID] = 0;
     return;
   }
@@ -207,7 +214,7 @@ cudaError_t launch_incremental(cupc_graph* g, const uint32_t* edges, const int8_
   cudaError_t e = cudaMemsetAsync(g->gc + GC_BATCH_DEL, 0, sizeof(uint32_t), s);
   if (e != cudaSuccess) return e;
   const int grid = (int)std::min<size_t>((n + 255) / 256, (size_t)g->sms * 8);
-  k_incr<<<grid, 256, 0, s>>>(edges, ops, n, g->V, g->label, g->ipar, g->forest_sorted, g->gc);
+  k_incr<<<grid, 256, 0, s>>>(edges, ops, n, g->V, g->label, g->ipar, g->forest_sorted, g->fdead, g->gc);
   k_incr_finish<<<(int)std::min<size_t>((g->V + 255) / 256, (size_t)g->sms * 4), 256, 0, s>>>(g->label, g->ipar,
                                                                                                 g->V, g->gc);
   return cudaGetLastError();

@@ -97,3 +97,37 @@ def test_incremental_off_by_default_and_switchable():
         if not on:  # off: every query after an update recovers
             assert dev.stats()["recoveries"] == n0 + 4
     assert C.cupc_set_incremental(None, 1, None) == C.CUPC_EINVAL
+
+
+def test_warm_start_after_forest_edge_deletes():
+    # delete-only batches: a deleted forest edge makes the next recovery
+    # start from the fragments of the remaining forest (round 0 samples
+    # fewer than V components); the graph falls apart over the batches and
+    # every answer still equals the oracle's full recovery
+    from paper_2509_14433_gb300 import cupc as C
+    from tests.test_gpu_parity import assert_same_recovery
+    V, seed = 600, 41
+    g = WL.rng(seed)
+    dev, ref = _dev(V, seed), O.Graph(V, seed)
+    assert C.cupc_set_incremental(dev.h, 1, None) == 0
+    E = WL.er_edges(V, 0.02, seed)
+    present = set(int(a) * V + int(b) for a, b in E)
+    assert dev.update(E) == 0 and ref.update(E) == O.OK
+    warm = 0
+    for k in range(25):
+        ids = np.array(sorted(present), np.int64)
+        pick = ids[g.choice(len(ids), min(len(ids), 120), replace=False)]
+        present.difference_update(int(x) for x in pick)
+        D = np.stack([pick // V, pick % V], 1).astype(np.uint32)
+        ops = -np.ones(len(D), np.int8)
+        assert dev.update(D, ops) == 0 and ref.update(D, ops) == O.OK
+        pairs = WL.uniform_pairs(V, 400, g, distinct=False)
+        s1, a1 = dev.query(pairs)
+        s2, a2 = ref.query(pairs)
+        assert s1 == s2 == 0 and np.array_equal(a1, a2), k
+        if dev.round_log()[0][0] < V:
+            warm += 1
+    assert warm > 0
+    assert np.array_equal(dev.labels(), ref.labels())
+    assert len(np.unique(ref.labels())) > 1  # the graph did fall apart
+    assert_same_recovery(dev, ref)
