@@ -285,8 +285,12 @@ cupc_status cupc_update_batch(cupc_graph* g, const uint32_t* edges, const int8_t
   const size_t B = g->max_batch;
   const bool dev_e = is_device_ptr(edges), dev_o = is_device_ptr(ops);
   if (dev_e && dev_o) {
-    CUPC_TRY(launch_validate(g, edges, ops, n, s));
-    for (size_t i = 0; i < n; i += B) CUPC_TRY(launch_update_chunk(g, edges + 2 * i, (n - i < B ? n - i : B), s));
+    if (n <= B) {
+      CUPC_TRY(launch_update_chunk(g, edges, n, s, ops));  // validated on the way
+    } else {
+      CUPC_TRY(launch_validate(g, edges, ops, n, s));
+      for (size_t i = 0; i < n; i += B) CUPC_TRY(launch_update_chunk(g, edges + 2 * i, (n - i < B ? n - i : B), s));
+    }
     if (g->inc) CUPC_TRY(launch_incremental(g, edges, ops, n, s));
     return mark_updated(g, s, true);
   } else if (!dev_e && !dev_o && n <= B) {
@@ -303,8 +307,7 @@ cupc_status cupc_update_batch(cupc_graph* g, const uint32_t* edges, const int8_t
     CUPC_TRY(cudaMemcpyAsync(so, ops, n, cudaMemcpyHostToDevice, g->copy_stream));
     CUPC_TRY(cudaEventRecord(g->slot_ready[k], g->copy_stream));
     CUPC_TRY(cudaStreamWaitEvent(s, g->slot_ready[k], 0));
-    CUPC_TRY(launch_validate(g, se, so, n, s));
-    CUPC_TRY(launch_update_chunk(g, se, n, s));
+    CUPC_TRY(launch_update_chunk(g, se, n, s, so));
     if (g->inc) CUPC_TRY(launch_incremental(g, se, so, n, s));
     CUPC_TRY(mark_slot_free(g, k, s));
     return mark_updated(g, s, true);
@@ -321,8 +324,7 @@ cupc_status cupc_update_batch(cupc_graph* g, const uint32_t* edges, const int8_t
     };
     if (n <= B) {
       CUPC_TRY(stage(0, n));
-      CUPC_TRY(launch_validate(g, g->stage_edges, g->stage_ops, n, s));
-      CUPC_TRY(launch_update_chunk(g, g->stage_edges, n, s));
+      CUPC_TRY(launch_update_chunk(g, g->stage_edges, n, s, g->stage_ops));
     } else {
       for (size_t i = 0; i < n; i += B) {
         size_t k = n - i < B ? n - i : B;

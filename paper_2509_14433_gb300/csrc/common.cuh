@@ -234,7 +234,10 @@ struct ProfScope {
 namespace cupc {
 // Launchers (defined in update.cu / recover.cu); all stream-ordered.
 cudaError_t launch_keys(cupc_graph* g, cudaStream_t s);
-cudaError_t launch_update_chunk(cupc_graph* g, const uint32_t* edges, size_t n, cudaStream_t s);
+// validate_ops: also validate this chunk (a batch of one chunk), else the
+// caller has validated the whole batch first.
+cudaError_t launch_update_chunk(cupc_graph* g, const uint32_t* edges, size_t n, cudaStream_t s,
+                                const int8_t* validate_ops = nullptr);
 cudaError_t launch_validate(cupc_graph* g, const uint32_t* edges, const int8_t* ops, size_t n, cudaStream_t s);
 cudaError_t setup_update(cupc_graph* g);
 cudaError_t configure_apply(cupc_graph* g);

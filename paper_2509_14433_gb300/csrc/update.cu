@@ -70,17 +70,30 @@ __global__ void k_count(const uint32_t* __restrict__ edges, size_t n, uint32_t* 
 // batch and counts its endpoints in a shared histogram of all V vertices, so
 // the global counters see one atomic per (CTA, vertex) instead of one per
 // record.
-__global__ void __launch_bounds__(1024) k_count_priv(const uint32_t* __restrict__ edges, size_t n, uint32_t V,
-                                                     uint32_t* cnt, const uint32_t* gc) {
+// With ops (a batch of one chunk) it also validates the batch as k_validate
+// does, saving that pass; counts of an invalid batch are cleared by
+// k_plan_write.
+__global__ void __launch_bounds__(1024) k_count_priv(const uint32_t* __restrict__ edges,
+                                                     const int8_t* __restrict__ ops, size_t n, uint32_t V,
+                                                     uint32_t* cnt, uint32_t* gc) {
   extern __shared__ uint32_t s_h[];  // V
   if (ld_cg(&gc[GC_ERR]) & kErrInval) return;
   for (uint32_t w = threadIdx.x; w < V; w += blockDim.x) s_h[w] = 0;
   __syncthreads();
   const size_t chunk = (n + gridDim.x - 1) / gridDim.x, lo = blockIdx.x * chunk, hi = min(n, lo + chunk);
+  bool bad = false;
   for (size_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-    atomicAdd(&s_h[edges[2 * i]], 1u);
-    atomicAdd(&s_h[edges[2 * i + 1]], 1u);
+    const uint32_t u = edges[2 * i], v = edges[2 * i + 1];
+    if (ops) {
+      const int8_t op = ops[i];
+      bad |= (u >= V) | (v >= V) | (u == v) | ((op != 1) & (op != -1));
+    }
+    if (u < V && v < V) {
+      atomicAdd(&s_h[u], 1u);
+      atomicAdd(&s_h[v], 1u);
+    }
   }
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(&gc[GC_ERR], kErrInval);
   __syncthreads();
   for (uint32_t w = threadIdx.x; w < V; w += blockDim.x) {
     const uint32_t c = s_h[w];
@@ -256,8 +269,12 @@ __global__ void __launch_bounds__(256) k_plan_write(uint32_t* cnt, uint32_t* cur
                                                     uint32_t vpt, uint32_t item_records, const uint4* __restrict__ part,
                                                     uint32_t apply_ctas, uint32_t* gc) {
   __shared__ uint32_t sw[3][32];
-  if (ld_cg(&gc[GC_ERR]) & kErrInval) return;
   const uint32_t nb = gridDim.x, b = blockIdx.x;
+  if (ld_cg(&gc[GC_ERR]) & kErrInval) {  // a dropped batch may have counted: start clean
+    const uint32_t lo = b * blockDim.x * vpt, hi = min(V, lo + blockDim.x * vpt);
+    for (uint32_t w = lo + threadIdx.x; w < hi; w += blockDim.x) cnt[w] = 0;
+    return;
+  }
   // offsets of this slice and the grand totals
   uint32_t before[3] = {0, 0, 0}, all[3] = {0, 0, 0};
   for (uint32_t j = threadIdx.x; j < nb; j += blockDim.x) {
@@ -428,7 +445,8 @@ cudaError_t configure_apply(cupc_graph* g) {
   return apply_config(g, g->item_records, g->R, g->apply_cps, &g->apply_smem, &g->apply_grid);
 }
 
-cudaError_t launch_update_chunk(cupc_graph* g, const uint32_t* edges, size_t n, cudaStream_t s) {
+cudaError_t launch_update_chunk(cupc_graph* g, const uint32_t* edges, size_t n, cudaStream_t s,
+                                const int8_t* validate_ops) {
   if (n == 0) return cudaSuccess;
   // the setting of this batch size's bucket, else the graph's default
   uint32_t ir = g->item_records, R = g->R;
@@ -442,13 +460,18 @@ cudaError_t launch_update_chunk(cupc_graph* g, const uint32_t* edges, size_t n, 
   }
   const int agrid = (int)std::min<size_t>(std::min<size_t>((size_t)grid_max, 2 * n), kPlanGridCap);
   int grid = (int)std::min<size_t>((n + 255) / 256, (size_t)g->sms * 8);
+  // dense batch on a small graph: group through shared histograms (and
+  // validate there); else validate in a pass of its own
+  const int pgrid = (int)std::min<size_t>((size_t)g->sms, 2 * n / ((size_t)kPrivPerVertex * g->V));
+  const bool priv = g->V <= kPrivMaxV && pgrid >= (int)kPrivMinCtas;
+  if (!priv && validate_ops) {
+    cudaError_t e = launch_validate(g, edges, validate_ops, n, s);
+    if (e != cudaSuccess) return e;
+  }
   {
     ProfScope ps(g, s, PC_GROUP, 4);
-    // dense batch on a small graph: group through shared histograms
-    const int pgrid = (int)std::min<size_t>((size_t)g->sms, 2 * n / ((size_t)kPrivPerVertex * g->V));
-    const bool priv = g->V <= kPrivMaxV && pgrid >= (int)kPrivMinCtas;
     if (priv)
-      k_count_priv<<<pgrid, 1024, 4 * g->V, s>>>(edges, n, g->V, g->cnt, g->gc);
+      k_count_priv<<<pgrid, 1024, 4 * g->V, s>>>(edges, validate_ops, n, g->V, g->cnt, g->gc);
     else
       k_count<<<grid, 256, 0, s>>>(edges, n, g->cnt, g->gc);
     const uint32_t vpt = plan_vpt(g->V), nb = (g->V + 256 * vpt - 1) / (256 * vpt);

@@ -226,6 +226,40 @@ def test_invalid_batch_is_dropped_whole_and_sticky(host):
     assert np.array_equal(dev.export(), ref.export())
 
 
+@pytest.mark.parametrize("host", [False, True])
+def test_large_invalid_batch_on_small_graph_is_dropped_whole(host):
+    # a batch of 2^16 edges on V=1000 is counted through shared histograms
+    # and validated in that same pass: one bad entry anywhere still drops
+    # the whole batch, leaves no counts behind, and the next batch is exact
+    V, n = 1000, 1 << 16
+    dev, ref = _dev(V, 9), O.Graph(V, 9)
+    E = WL.er_edges(V, 0.3, 9)
+    E = E[WL.rng(9).permutation(len(E))]
+    first, second = E[:n], E[n:2 * n]
+    assert dev.update(first, host=host) == 0 and ref.update(first) == O.OK
+    before = dev.export()
+    for pos, fix in ((n - 1, "loop"), (n // 2, "op"), (0, "range"), (12345, "range_u")):
+        e, o = second.copy(), np.ones(n, np.int8)
+        if fix == "loop":
+            e[pos, 1] = e[pos, 0]
+        elif fix == "op":
+            o[pos] = 0
+        elif fix == "range":
+            e[pos, 1] = V
+        else:
+            e[pos, 0] = 0xFFFFFFFF
+        dev.update(e, o, host=host)
+        if host:
+            torch.cuda.synchronize()
+        assert np.array_equal(dev.export(), before), fix
+        assert dev.sync() == 1 and dev.sync() == 0
+    assert dev.update(second, host=host) == 0 and ref.update(second) == O.OK
+    assert dev.sync() == 0
+    assert np.array_equal(dev.export(), ref.export())
+    pairs = WL.uniform_pairs(V, 300, WL.rng(10), distinct=False)
+    assert np.array_equal(dev.query(pairs)[1], ref.query(pairs)[1])
+
+
 def test_query_pair_out_of_range():
     V = 30
     dev = _dev(V, 1)
