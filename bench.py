@@ -162,17 +162,24 @@ class Clocks:
 
 def oracle_sample(E, batches=CPU_SAMPLE_BATCHES, seed=SEED):
     """CPU oracle on a bounded sample: the first `batches` insert batches of
-    the dense stream, then the spanning forest (one thread)."""
+    the dense stream, one 1k-pair Connected batch (which runs the recovery),
+    then the spanning forest (one thread). Returns the updates, the time of
+    the whole sample and the time of the query batch."""
     import oracle as O
     n = batches * BATCH
+    pairs = WL.uniform_pairs(V_DENSE, 1000, WL.rng(seed + 7), distinct=False)
     g = O.Graph(V_DENSE, seed)
     t = time.perf_counter()
     for i in range(0, n, BATCH):
         assert g.update(E[i:i + BATCH]) == O.OK
+    tq = time.perf_counter()
+    s, a = g.query(pairs)
+    tq = time.perf_counter() - tq
+    assert s in (O.OK, O.EINCOMPLETE)
     s, f = g.spanning_forest()
     dt = time.perf_counter() - t
     g.close()
-    return n, dt
+    return n, dt, tq
 
 
 def run_reference(args):
@@ -182,10 +189,11 @@ def run_reference(args):
     E, D = make_dense_stream()
     for _ in range(args.warmup):
         oracle_sample(E, REF_SAMPLE_BATCHES)
-    times, n = [], 0
+    times, qtimes, n = [], [], 0
     for _ in range(args.steps):
-        n, dt = oracle_sample(E, REF_SAMPLE_BATCHES)
+        n, dt, tq = oracle_sample(E, REF_SAMPLE_BATCHES)
         times.append(dt)
+        qtimes.append(tq)
     tot = sum(times)
     val = n * args.steps / tot
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
@@ -193,7 +201,9 @@ def run_reference(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
             "data": "synthetic", "config": workload_config(len(E), len(D)),
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"first {n} inserts of the dense stream + spanning forest per step"},
+                             "sample": f"first {n} inserts of the dense stream + one 1k-pair Connected "
+                                       "batch + spanning forest per step",
+                             "query_batch_ms_p50": 1e3 * float(np.median(qtimes))},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -349,9 +359,11 @@ def run_gpu(args):
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        n, dt = oracle_sample(E)
+        n, dt, tq = oracle_sample(E)
         cpu = {"value": n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"first {n} inserts of the dense stream + spanning forest (single thread)"}
+               "sample": f"first {n} inserts of the dense stream + one 1k-pair Connected batch + spanning "
+                         "forest (single thread)",
+               "query_batch_ms": 1e3 * tq}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -575,67 +587,86 @@ def serving_compare(torch, C, dev, n_graphs=64, upd_range=(5e4, 5e5), seed=5):
     return out
 
 
-def paper_stream(torch, C, dev, stream, n_upd=1 << 21):
-    """The paper's stream shape on a K13-sized dense graph (context for its
-    published numbers, not the headline workload): V = 2^13, ER(0.5) edges
-    (about the K13 density) in a seeded random order, inserted one burst of
-    rho ~ U[1000, 2000] updates at a time, each followed by rho/9 uniform
-    Connected pairs (10% of the operations are queries). The first n_upd
-    updates of the standard stream (insert all, then delete all) are run,
-    with a full recovery per query burst and with incremental labels
-    (cupc_set_incremental): updates/s and queries/s over the whole prefix,
-    and the latency of a sampled burst (its update batch and its queries,
-    host submit -> answers ready)."""
-    V, g_rng = 1 << 13, WL.rng(13)
-    E = WL.er_edges(V, 0.5, 13)
-    E = E[g_rng.permutation(len(E))][:n_upd]
-    bursts = []
-    i = 0
-    while i < len(E):
-        rho = int(g_rng.integers(1000, 2001))
-        bursts.append((i, min(rho, len(E) - i), max(1, rho // 9)))
-        i += rho
-    n_q = sum(b[2] for b in bursts)
-    E_d = torch.from_numpy(E.reshape(-1)).to(dev)
-    ins_d = torch.ones(len(E), dtype=torch.int8, device=dev)
-    P_d = torch.from_numpy(WL.uniform_pairs(V, n_q, g_rng, distinct=False).reshape(-1)).to(dev)
-    out_d = torch.empty(n_q, dtype=torch.uint8, device=dev)
+def paper_stream(torch, C, dev, stream):
+    """The paper's two stream shapes on a K13-sized dense graph (context for
+    its published numbers, not the headline workload): V = 2^13, ER(0.5)
+    edges (about the K13 density). The standard stream inserts every edge,
+    then deletes every edge; the fixed forest stream inserts one spanning
+    forest, then inserts every other edge and deletes it again (one cycle).
+    Updates arrive in bursts of rho ~ U[1000, 2000], each followed by rho/9
+    uniform Connected pairs (10% of the operations are queries). Each whole
+    stream runs with a full recovery per query burst and with incremental
+    labels (cupc_set_incremental): updates/s and queries/s over the stream,
+    the recoveries it ran, and the latency of every 25th burst (its update
+    batch and its queries, host submit -> answers ready)."""
+    V = 1 << 13
+    paper = {"standard": ("K13", 1.79e6, 3.37e6), "fixed_forest": ("K13-FF", 4.56e6, 6.92e6)}
+    res = {"workload": "V=8192 ER(0.5), whole streams, query bursts of rho/9 pairs every rho ~ U[1000,2000] "
+                       "updates", "paper_cupcake_48core_epyc": {}}
     st, g = C.cupc_init(V, 1, None, None, stream)
     C.check(st)
+    stats = np.zeros(8, np.uint64)
 
-    def run(sample_every=0):
-        lat, q = [], 0
-        for k, (i, n, m) in enumerate(bursts):
-            sample = sample_every and k % sample_every == sample_every - 1
-            if sample:
-                torch.cuda.synchronize()
-                t = time.perf_counter()
-            C.check(C.cupc_update_batch(g, E_d[2 * i:], ins_d[i:], n, stream))
-            C.check(C.cupc_query(g, P_d[2 * q:], m, out_d[q:], stream))
-            if sample:
-                torch.cuda.synchronize()
-                lat.append((time.perf_counter() - t) * 1e6)
-            q += m
-        return lat
+    def recoveries():
+        C.check(C.cupc_stats(g, stats, stream))
+        return int(stats[5])
 
-    res = {"workload": f"V=8192 ER(0.5) random-order inserts, first {len(E)} updates, query bursts of rho/9 "
-                       "pairs every rho ~ U[1000,2000] updates", "bursts": len(bursts),
-           "paper_cupcake_k13_std_48core_epyc": {"updates_per_s": 1.79e6, "queries_per_s": 3.37e6}}
-    for mode, inc in (("recovery_per_burst", 0), ("incremental_labels", 1)):
-        C.check(C.cupc_set_incremental(g, inc, stream))
-        C.check(C.cupc_reset(g, stream))
-        run()  # warm-up pass
-        C.check(C.cupc_reset(g, stream))
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        run()
-        torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
-        C.check(C.cupc_reset(g, stream))
-        lat = run(sample_every=25)
-        res[mode] = {"updates_per_s": len(E) / dt, "queries_per_s": n_q / dt,
-                     "burst_latency_p50_us": statistics.median(lat),
-                     "burst_latency_p99_us": float(np.percentile(lat, 99))}
+    for shape in ("standard", "fixed_forest"):
+        if shape == "standard":
+            E, ops = WL.standard_stream(V, 0.5, 13)
+        else:
+            E, ops, _ = WL.fixed_forest_stream(V, 0.5, 13, cycles=1)
+        g_rng = WL.rng(17)
+        bursts, i = [], 0
+        while i < len(E):
+            rho = int(g_rng.integers(1000, 2001))
+            bursts.append((i, min(rho, len(E) - i), max(1, rho // 9)))
+            i += rho
+        n_q = sum(b[2] for b in bursts)
+        E_d = torch.from_numpy(E.reshape(-1)).to(dev)
+        ops_d = torch.from_numpy(ops).to(dev)
+        P_d = torch.from_numpy(WL.uniform_pairs(V, n_q, g_rng, distinct=False).reshape(-1)).to(dev)
+        out_d = torch.empty(n_q, dtype=torch.uint8, device=dev)
+
+        def run(todo, sample_every=0):
+            lat, q = [], 0
+            for k, (i, n, m) in enumerate(todo):
+                sample = sample_every and k % sample_every == sample_every - 1
+                if sample:
+                    torch.cuda.synchronize()
+                    t = time.perf_counter()
+                C.check(C.cupc_update_batch(g, E_d[2 * i:], ops_d[i:], n, stream))
+                C.check(C.cupc_query(g, P_d[2 * q:], m, out_d[q:], stream))
+                if sample:
+                    torch.cuda.synchronize()
+                    lat.append((time.perf_counter() - t) * 1e6)
+                q += m
+            return lat
+
+        name, pu, pq = paper[shape]
+        res["paper_cupcake_48core_epyc"][name] = {"updates_per_s": pu, "queries_per_s": pq}
+        out = {"updates": len(E), "inserts": int(np.sum(ops == 1)), "deletes": int(np.sum(ops == -1)),
+               "queries": n_q, "bursts": len(bursts)}
+        for mode, inc in (("recovery_per_burst", 0), ("incremental_labels", 1)):
+            C.check(C.cupc_set_incremental(g, inc, stream))
+            C.check(C.cupc_reset(g, stream))
+            run(bursts[:64])  # warm-up
+            C.check(C.cupc_reset(g, stream))
+            r0 = recoveries()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            run(bursts)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            nrec = recoveries() - r0
+            C.check(C.cupc_reset(g, stream))
+            lat = run(bursts, sample_every=25)
+            out[mode] = {"updates_per_s": len(E) / dt, "queries_per_s": n_q / dt, "recoveries": nrec,
+                         "burst_latency_p50_us": statistics.median(lat),
+                         "burst_latency_p99_us": float(np.percentile(lat, 99))}
+        res[shape] = out
+        del E_d, ops_d, P_d, out_d
+    C.check(C.cupc_sync(g, stream), "paper stream", ok=(C.CUPC_OK, C.CUPC_EINCOMPLETE))
     C.cupc_destroy(g)
     return res
 

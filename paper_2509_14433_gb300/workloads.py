@@ -103,6 +103,53 @@ def dense_stream(V: int = 16384, p: float = 0.5, batch: int = 1 << 20,
     return e, n_del, order
 
 
+def standard_stream(V: int, p: float, seed: int):
+    """The standard stream of a static ER(p) graph, as in the paper's
+    experiments (§6, datasets): insert every edge, then delete every edge,
+    each phase in its own seeded random order. Returns edges [2E, 2] uint32
+    and ops [2E] int8."""
+    e = er_edges(V, p, seed)
+    g = rng(seed + 3000)
+    ins, dels = e[g.permutation(len(e))], e[g.permutation(len(e))]
+    ops = np.concatenate([np.ones(len(e), np.int8), -np.ones(len(e), np.int8)])
+    return np.concatenate([ins, dels]), ops
+
+
+def spanning_forest_edges(V: int, e: np.ndarray, g: np.random.Generator) -> np.ndarray:
+    """One spanning forest of the graph (V, e): the minimum spanning forest
+    under seeded random distinct weights, so that it is unrelated to edge
+    ids. [F, 2] uint32 rows u < v, F = V - #components."""
+    import scipy.sparse as sp
+    from scipy.sparse.csgraph import minimum_spanning_tree
+    if len(e) == 0:
+        return np.zeros((0, 2), np.uint32)
+    w = g.permutation(len(e)).astype(np.float64) + 1.0
+    t = minimum_spanning_tree(sp.csr_matrix((w, (e[:, 0], e[:, 1])), shape=(V, V))).tocoo()
+    f = np.stack([np.minimum(t.row, t.col), np.maximum(t.row, t.col)], 1).astype(np.uint32)
+    return f[g.permutation(len(f))]
+
+
+def fixed_forest_stream(V: int, p: float, seed: int, cycles: int = 1):
+    """The fixed forest stream of a static ER(p) graph, as in the paper's
+    experiments (§6 and App. C, datasets): insert the edges of one spanning
+    forest, then ``cycles`` times insert every other edge and delete them
+    all again, each pass in a fresh seeded random order. The forest is never
+    deleted, so most updates are non-tree updates. Returns edges [n, 2]
+    uint32, ops [n] int8 and the number of forest edges (the first ones)."""
+    e = er_edges(V, p, seed)
+    g = rng(seed + 4000)
+    f = spanning_forest_edges(V, e, g)
+    fid = np.sort(f[:, 0].astype(np.int64) * V + f[:, 1])
+    eid = e[:, 0].astype(np.int64) * V + e[:, 1]
+    pos = np.minimum(np.searchsorted(fid, eid), max(0, len(fid) - 1))
+    rest = e[fid[pos] != eid] if len(fid) else e
+    parts, ops = [f], [np.ones(len(f), np.int8)]
+    for _ in range(cycles):
+        parts += [rest[g.permutation(len(rest))], rest[g.permutation(len(rest))]]
+        ops += [np.ones(len(rest), np.int8), -np.ones(len(rest), np.int8)]
+    return np.concatenate(parts), np.concatenate(ops), len(f)
+
+
 def final_edge_set(V: int, steps) -> np.ndarray:
     """Edge ids u*V+v present after applying every update step (toggle
     semantics), sorted ascending."""

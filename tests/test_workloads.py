@@ -2,6 +2,7 @@
 insert names an absent edge and a delete a present one): every batch is
 replayed against a set of present edges, update by update."""
 import numpy as np
+import pytest
 
 from paper_2509_14433_gb300 import workloads as WL
 
@@ -48,3 +49,44 @@ def test_toggle_and_dense_streams_are_valid():
     dels = Ed[order[:n_del]]
     assert n_del == round(0.1 * len(Ed))
     _replay([(Ed, np.ones(len(Ed), np.int8)), (dels, -np.ones(len(dels), np.int8))], V)
+
+
+def _components(V, E):
+    sp = pytest.importorskip("scipy.sparse")
+    from scipy.sparse.csgraph import connected_components
+    E = np.asarray(E, np.int64).reshape(-1, 2)
+    A = sp.csr_matrix((np.ones(len(E)), (E[:, 0], E[:, 1])), shape=(V, V))
+    return connected_components(A, directed=False)
+
+
+def test_standard_stream_inserts_all_then_deletes_all():
+    V = 120
+    E, ops = WL.standard_stream(V, 0.1, 4)
+    n = len(E) // 2
+    assert np.all(ops[:n] == 1) and np.all(ops[n:] == -1)
+    assert _replay([(E, ops)], V) == set()
+    ins = set((E[:n, 0].astype(np.int64) * V + E[:n, 1]).tolist())
+    assert ins == set((WL.er_edges(V, 0.1, 4)[:, 0].astype(np.int64) * V + WL.er_edges(V, 0.1, 4)[:, 1]).tolist())
+    assert not np.array_equal(E[:n], E[n:])  # each phase has its own order
+
+
+def test_fixed_forest_stream_keeps_a_spanning_forest():
+    V, p = 150, 0.02  # sparse: several components and isolated vertices
+    E, ops, nf = WL.fixed_forest_stream(V, p, 6, cycles=2)
+    static = WL.er_edges(V, p, 6)
+    ncomp, lab = _components(V, static)
+    F = E[:nf]
+    assert np.all(ops[:nf] == 1) and nf == V - ncomp
+    # the forest spans the static graph's components (V - ncomp acyclic edges)
+    ncf, labf = _components(V, F)
+    assert ncf == ncomp and np.array_equal(lab[F[:, 0]], lab[F[:, 1]])
+    for a in range(ncomp):  # same partition
+        assert len(set(labf[lab == a].tolist())) == 1
+    # then every other edge is inserted and deleted, twice; the forest stays
+    rest = len(static) - nf
+    assert len(E) == nf + 4 * rest
+    present = _replay([(E, ops)], V)
+    assert present == set((F[:, 0].astype(np.int64) * V + F[:, 1]).tolist())
+    for k in range(4):
+        seg = slice(nf + k * rest, nf + (k + 1) * rest)
+        assert np.all(ops[seg] == (1 if k % 2 == 0 else -1))
