@@ -2,8 +2,9 @@
 // Algorithm": an update of edge (u,v) updates every sketch of u and of v;
 // Theorem A.2: CameoSketch touches one bucket per column per update).
 //
-// One chunk of <= max_batch edges (validated first by k_validate) goes
-// through five stream-ordered kernels:
+// One chunk of <= max_batch edges goes through five stream-ordered kernels
+// (a batch is validated whole by k_validate first, or, when it is one chunk
+// that k_count_priv counts, inside k_count_priv):
 //   k_count   per-vertex record counts (2 records per edge, one per
 //             endpoint); k_count_priv for dense batches on small graphs,
 //             through per-CTA shared histograms
