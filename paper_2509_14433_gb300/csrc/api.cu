@@ -56,8 +56,14 @@ struct Layout {
   size_t sketch, keys, gc, cnt, cursor, rec, recw, items, part, stage_edges, stage_ops, stage_edges1, stage_ops1,
       label, parent, minv, rcnt, roff,
       perm, permb, pcount, final_, merged, best, best2, cand, forest, forest_sorted, acc, log_ids, log_live,
-      log_ncand, hlist, ipar, fdead, total;
+      log_ncand, hlist, ipar, fdead, fadd, fadd_dead, ftab, ftab_pos, total;
 };
+
+// Slots of the incremental merge-edge table: at least 2V, a power of two.
+uint32_t ftab_bits(uint32_t V) {
+  const uint32_t b = ceil_log2(V) + 1;
+  return b < 6 ? 6 : b;
+}
 
 Layout layout(const Dims& d) {
   Layout l{};
@@ -104,6 +110,11 @@ Layout layout(const Dims& d) {
   l.hlist = take(kSmallHook * sizeof(ulonglong2));
   l.ipar = take(V * 4);
   l.fdead = take(V);
+  l.fadd = take(V * 8);
+  l.fadd_dead = take(V);
+  const size_t T = (size_t)1 << ftab_bits(d.V);
+  l.ftab = take(T * 8);
+  l.ftab_pos = take(T * 4);
   l.total = off;
   return l;
 }
@@ -236,6 +247,11 @@ cupc_status cupc_init(uint32_t V, uint64_t seed, const cupc_params* params, void
   g->hlist = (ulonglong2*)(b + l.hlist);
   g->ipar = (uint32_t*)(b + l.ipar);
   g->fdead = (uint8_t*)(b + l.fdead);
+  g->fadd = (uint64_t*)(b + l.fadd);
+  g->fadd_dead = (uint8_t*)(b + l.fadd_dead);
+  g->ftab = (uint64_t*)(b + l.ftab);
+  g->ftab_pos = (uint32_t*)(b + l.ftab_pos);
+  g->ftab_bits = ftab_bits(d.V);
   if (setup_update(g) != cudaSuccess || setup_recover(g) != cudaSuccess) {
     cudaGetLastError();
     return fail(CUPC_ECUDA);

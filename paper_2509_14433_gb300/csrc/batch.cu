@@ -378,8 +378,15 @@ cupc_status cupc_batcher_update(cupc_batcher* b, cupc_graph* const* graphs, cons
   if (e != cudaSuccess) return CUPC_ECUDA;
   if (cudaEventRecord(b->used[slot], s) != cudaSuccess) return CUPC_ECUDA;
   b->cur ^= 1;
-  for (uint32_t i = 0; i < k; i++)
-    if (n[i]) graphs[i]->dirty = true;
+  // like cupc_update_batch: the next query recovers; the batcher does not
+  // follow incremental labels, so a graph in that mode drops them
+  for (uint32_t i = 0; i < k; i++) {
+    if (!n[i]) continue;
+    graphs[i]->dirty = true;
+    graphs[i]->forest_stale = true;
+    if (graphs[i]->inc && cudaMemsetAsync(graphs[i]->gc + GC_LABELS_VALID, 0, sizeof(uint32_t), s) != cudaSuccess)
+      return CUPC_ECUDA;
+  }
   return CUPC_OK;
 }
 

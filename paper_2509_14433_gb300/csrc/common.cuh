@@ -88,10 +88,11 @@ enum : uint32_t {
   GC_REC_DIRTY = 20, // a recovery gave up at a barrier: its scratch may be non-zero
   GC_LABELS_VALID = 21,  // incremental mode: labels hold the current graph's components
   GC_FOREST_SORTED = 22, // forest_sorted holds the last recovery's forest
-  GC_INC_MERGES = 23,    // incremental merges since the last recovery
   GC_BATCH_DEL = 24,     // the current batch deletes an edge (incremental mode)
-  GC_WARM = 25,          // incremental mode: forest edges were deleted, no merges: warm-start recovery
+  GC_WARM = 25,          // incremental mode: forest edges were deleted: warm-start recovery
   GC_NSORTED = 26,       // length of forest_sorted
+  GC_NFADD = 27,         // incremental mode: merge edges recorded in fadd since the last recovery
+  GC_BATCH_MERGE = 28,   // the current batch merged two components (incremental mode)
   GC_SLOTS = 32
 };
 
@@ -192,6 +193,13 @@ struct cupc_graph {
   ulonglong2* hlist;    // kSmallHook: crossing candidates of a hook step (recovery)
   uint32_t* ipar;       // V: union-find over labels for incremental inserts
   uint8_t* fdead;       // V: forest_sorted[i] was deleted since the last recovery
+  // incremental mode: the inserts that merged two components since the last
+  // recovery (forest edges the stream added), and a hash table of their ids
+  uint64_t* fadd;       // V
+  uint8_t* fadd_dead;   // V: fadd[j] was deleted since
+  uint64_t* ftab;       // 2^ftab_bits ids (0 = empty slot; no edge has id 0)
+  uint32_t* ftab_pos;   // 2^ftab_bits: the fadd index of ftab's id
+  uint32_t ftab_bits;
   cupc_status last_recovery;
   // profiling: (kernel class, start, stop, launches) per recorded launch group
   struct ProfRec {

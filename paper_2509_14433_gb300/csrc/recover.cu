@@ -45,6 +45,10 @@ struct RecArgs {
   uint32_t* ipar;     // V: union-find of incremental inserts, identity after a recovery
   const uint64_t* forest_sorted;
   uint8_t* fdead;     // V: forest_sorted[i] deleted since the last recovery
+  const uint64_t* fadd;      // V: forest edges added by incremental merges since
+  const uint8_t* fadd_dead;  // V: fadd[j] deleted since
+  unsigned long long* ftab;  // 2^ftab_bits: the ids of fadd (cleared here)
+  uint32_t ftab_bits;
   uint32_t inc, force;  // incremental mode; run even if the labels are valid
   uint32_t* gc;
 };
@@ -357,12 +361,13 @@ __global__ void __launch_bounds__(kRecThreads, 2) k_recover(RecArgs a) {
 
   // incremental mode: the updates since the last recovery kept the labels
   // exact (see k_incr), so there is nothing to recover; or they deleted
-  // forest edges and merged nothing: then the components are unions of the
-  // fragments of the remaining forest, and Boruvka starts from those
-  // (warm start) instead of from single vertices
+  // forest edges (of the recovered forest, or added by merges since): then
+  // the components are unions of the fragments of the remaining forest, and
+  // Boruvka starts from those (warm start) instead of from single vertices
   const bool valid = ld_cg(&gc[GC_LABELS_VALID]) != 0, warm = !a.force && valid && ld_cg(&gc[GC_WARM]) != 0;
   if (!a.force && valid && !warm) return;
-  const uint32_t nsorted = warm ? ld_cg(&gc[GC_NSORTED]) : 0;
+  const uint32_t nsorted = warm ? min(ld_cg(&gc[GC_NSORTED]), V) : 0;
+  const uint32_t nadd = warm ? min(ld_cg(&gc[GC_NFADD]), V) : 0;
   // after a recovery that gave up at a barrier, the reduce accumulators and
   // the last-arriver counters may hold partial sums: clear them first
   const bool dirty = ld_cg(&gc[GC_REC_DIRTY]) != 0;
@@ -382,10 +387,11 @@ __global__ void __launch_bounds__(kRecThreads, 2) k_recover(RecArgs a) {
   }
   if (dirty)
     for (size_t i = gtid; i < (size_t)V * W; i += gstride) a.acc[i] = make_ulonglong2(0, 0);
+  if (a.inc)  // the merge-edge table starts empty (fadd itself is read by a warm start below)
+    for (size_t i = gtid; i < ((size_t)1 << a.ftab_bits); i += gstride) a.ftab[i] = 0ull;
   if (gtid == 0) {
     gc[GC_LABELS_VALID] = 0;
     gc[GC_FOREST_SORTED] = 0;
-    gc[GC_INC_MERGES] = 0;
     gc[GC_WARM] = 0;
     gc[GC_NLIVE] = 0;
     gc[GC_NFOREST] = 0;
@@ -406,18 +412,31 @@ __global__ void __launch_bounds__(kRecThreads, 2) k_recover(RecArgs a) {
     a.log_ncand[r] = 0;
   }
   CUPC_GRID_SYNC();
-  if (dirty && gtid == 0) gc[GC_REC_DIRTY] = 0;  // every CTA has read it
+  if (gtid == 0) {  // every CTA has read them
+    if (dirty) gc[GC_REC_DIRTY] = 0;
+    gc[GC_NFADD] = 0;
+  }
   if (warm) {
     // fragments: union the endpoints of the forest edges still present (the
-    // larger root under the smaller), which also start the new forest
-    for (uint32_t base = gwarp * 32; base < nsorted; base += nwarps * 32) {
+    // larger root under the smaller): the recovered forest's, then those
+    // merges added. An edge whose union joins two fragments starts the new
+    // forest (all of them with a valid stream; at most V - 1 in any case).
+    const uint32_t nall = nsorted + nadd;
+    for (uint32_t base = gwarp * 32; base < nall; base += nwarps * 32) {
       const uint32_t i = base + lane;
-      const bool keep = i < nsorted && !a.fdead[i];
+      bool keep = false;
       uint64_t e = 0;
-      if (keep) {
+      if (i < nsorted) {
+        keep = !a.fdead[i];
         e = a.forest_sorted[i];
+      } else if (i < nall) {
+        keep = !a.fadd_dead[i - nsorted];
+        e = a.fadd[i - nsorted];
+      }
+      if (keep) {
         uint32_t x = (uint32_t)(e / V), y = (uint32_t)(e % V);
-        for (uint32_t k = 0; k < V; k++) {  // bounded: each failed CAS is another thread's progress
+        keep = false;
+        for (uint32_t k = 0; k < V && x < V && y < V; k++) {  // bounded: each failed CAS is another thread's progress
           x = find_root(a.parent, x, V);
           y = find_root(a.parent, y, V);
           if (x == y) break;
@@ -426,7 +445,10 @@ __global__ void __launch_bounds__(kRecThreads, 2) k_recover(RecArgs a) {
             x = y;
             y = t;
           }
-          if (atomicCAS(&a.parent[y], y, x) == y) break;
+          if (atomicCAS(&a.parent[y], y, x) == y) {
+            keep = true;
+            break;
+          }
         }
       }
       const uint32_t m = __ballot_sync(0xffffffffu, keep);
@@ -890,6 +912,10 @@ cudaError_t launch_recover(cupc_graph* g, cudaStream_t s, bool force) {
   a.ipar = g->ipar;
   a.forest_sorted = g->forest_sorted;
   a.fdead = g->fdead;
+  a.fadd = g->fadd;
+  a.fadd_dead = g->fadd_dead;
+  a.ftab = (unsigned long long*)g->ftab;
+  a.ftab_bits = g->ftab_bits;
   a.inc = g->inc ? 1u : 0u;
   a.force = force ? 1u : 0u;
   a.gc = g->gc;

@@ -141,15 +141,18 @@ __global__ void __launch_bounds__(1024) k_scatter_priv(const uint32_t* __restric
 // ---- incremental labels (cupc_set_incremental). After a complete
 // recovery the labels are the components of the graph; with a valid stream
 // (inserts of absent edges, deletes of present ones) an insert can only
-// merge two components, and deleting an edge outside the recovered spanning
-// forest cannot split one. So a batch keeps the labels exact by merging the
-// endpoint labels of its inserts (union-find over labels, the larger root
-// under the smaller, so a root is its component's minimum vertex id, the
-// label a recovery gives). A deleted forest edge is marked (fdead) and sets
-// GC_WARM: the next recovery starts from the fragments of the remaining
-// forest. A batch that deletes anything once an insert has merged components
-// since the recovery, or merges after forest edges were deleted, clears
-// GC_LABELS_VALID and the next query recovers in full.
+// merge two components, and deleting an edge outside a spanning forest of
+// the graph cannot split one. So a batch keeps the labels exact by merging
+// the endpoint labels of its inserts (union-find over labels, the larger
+// root under the smaller, so a root is its component's minimum vertex id,
+// the label a recovery gives). Each insert whose link succeeds joins two
+// components: it becomes a forest edge (fadd, with a hash table of ids), so
+// the recovered forest plus these edges stays a spanning forest of the
+// graph. A deleted forest edge of either kind is marked (fdead, fadd_dead)
+// and sets GC_WARM: the next recovery starts from the fragments of the
+// remaining forest. A batch that both merges and deletes clears
+// GC_LABELS_VALID (its order inside the batch is not followed) and the next
+// query recovers in full.
 __device__ __forceinline__ uint32_t inc_find(uint32_t* par, uint32_t x, uint32_t V) {
   for (uint32_t k = 0; k < V; k++) {  // a path is shorter than V
     const uint32_t y = ld_cg(&par[x]);
@@ -161,42 +164,89 @@ __device__ __forceinline__ uint32_t inc_find(uint32_t* par, uint32_t x, uint32_t
   return x;
 }
 
-__global__ void k_incr(const uint32_t* __restrict__ edges, const int8_t* __restrict__ ops, size_t n, uint32_t V,
-                       const uint32_t* __restrict__ label, uint32_t* ipar, const uint64_t* __restrict__ forest_sorted,
-                       uint8_t* fdead, uint32_t* gc) {
+// Home slot of an edge id in the merge-edge table (Fibonacci hashing).
+__device__ __forceinline__ uint32_t ftab_home(uint64_t id, uint32_t bits) {
+  return (uint32_t)((id * 0x9E3779B97F4A7C15ull) >> (64 - bits));
+}
+
+struct IncArgs {
+  const uint32_t* label;
+  uint32_t* ipar;
+  const uint64_t* forest_sorted;
+  uint8_t* fdead;
+  uint64_t* fadd;
+  uint8_t* fadd_dead;
+  unsigned long long* ftab;
+  uint32_t* ftab_pos;
+  uint32_t ftab_bits, V;
+  uint32_t* gc;
+};
+
+__global__ void k_incr(const uint32_t* __restrict__ edges, const int8_t* __restrict__ ops, size_t n, IncArgs a) {
+  uint32_t* gc = a.gc;
   if ((ld_cg(&gc[GC_ERR]) & kErrInval) || !ld_cg(&gc[GC_LABELS_VALID])) return;
-  const uint32_t nf = ld_cg(&gc[GC_NSORTED]);
+  const uint32_t V = a.V, nf = ld_cg(&gc[GC_NSORTED]), nadd = ld_cg(&gc[GC_NFADD]);
+  const uint32_t mask = (1u << a.ftab_bits) - 1u;
   bool del = false, merged = false, cut = false, warm = false;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
     const uint32_t u = edges[2 * i], v = edges[2 * i + 1];
+    const uint64_t id = (uint64_t)min(u, v) * V + max(u, v);
     if (ops[i] < 0) {
       del = true;
-      const uint64_t id = (uint64_t)min(u, v) * V + max(u, v);
-      uint32_t lo = 0, hi = nf;  // first forest id >= id
+      uint32_t lo = 0, hi = nf;  // first recovered forest id >= id
       while (lo < hi) {
         const uint32_t mid = (lo + hi) >> 1;
-        if (forest_sorted[mid] < id)
+        if (a.forest_sorted[mid] < id)
           lo = mid + 1;
         else
           hi = mid;
       }
-      if (lo < nf && forest_sorted[lo] == id) {
-        fdead[lo] = 1;
+      if (lo < nf && a.forest_sorted[lo] == id) {
+        a.fdead[lo] = 1;
         warm = true;
+      } else if (nadd) {  // a forest edge added by a merge?
+        uint32_t sl = ftab_home(id, a.ftab_bits);
+        for (uint32_t k = 0; k <= mask; k++, sl = (sl + 1) & mask) {
+          const unsigned long long key = ld_cg((const uint64_t*)&a.ftab[sl]);
+          if (key == 0ull) break;
+          if (key == (unsigned long long)id) {
+            const uint32_t j = ld_cg(&a.ftab_pos[sl]);
+            if (j < V) a.fadd_dead[j] = 1;
+            warm = true;
+            break;
+          }
+        }
       }
     } else {
-      uint32_t a = label[u], b = label[v];
+      uint32_t x = a.label[u], y = a.label[v];
       for (uint32_t k = 0; k < (1u << 20); k++) {  // bounded retries; giving up clears the labels
-        a = inc_find(ipar, a, V);
-        b = inc_find(ipar, b, V);
-        if (a == b) break;
-        if (a > b) {
-          const uint32_t t = a;
-          a = b;
-          b = t;
+        x = inc_find(a.ipar, x, V);
+        y = inc_find(a.ipar, y, V);
+        if (x == y) break;
+        if (x > y) {
+          const uint32_t t = x;
+          x = y;
+          y = t;
         }
-        if (atomicCAS(&ipar[b], b, a) == b) {
+        if (atomicCAS(&a.ipar[y], y, x) == y) {
           merged = true;
+          // this insert joined two components: record it as a forest edge
+          const uint32_t j = atomicAdd(&gc[GC_NFADD], 1u);
+          bool placed = false;
+          if (j < V) {
+            a.fadd[j] = id;
+            a.fadd_dead[j] = 0;
+            uint32_t sl = ftab_home(id, a.ftab_bits);
+            for (uint32_t q = 0; q <= mask; q++, sl = (sl + 1) & mask) {
+              const unsigned long long prev = atomicCAS(&a.ftab[sl], 0ull, (unsigned long long)id);
+              if (prev == 0ull || prev == (unsigned long long)id) {
+                a.ftab_pos[sl] = j;
+                placed = true;
+                break;
+              }
+            }
+          }
+          if (!placed) cut = true;  // cannot happen with a valid stream
           break;
         }
         if (k + 1 == (1u << 20)) cut = true;
@@ -205,20 +255,18 @@ __global__ void k_incr(const uint32_t* __restrict__ edges, const int8_t* __restr
   }
   if (__any_sync(0xffffffffu, cut) && (threadIdx.x & 31) == 0) gc[GC_LABELS_VALID] = 0;
   if (__any_sync(0xffffffffu, del) && (threadIdx.x & 31) == 0) gc[GC_BATCH_DEL] = 1;
-  if (__any_sync(0xffffffffu, merged) && (threadIdx.x & 31) == 0) gc[GC_INC_MERGES] = 1;
+  if (__any_sync(0xffffffffu, merged) && (threadIdx.x & 31) == 0) gc[GC_BATCH_MERGE] = 1;
   if (__any_sync(0xffffffffu, warm) && (threadIdx.x & 31) == 0) gc[GC_WARM] = 1;
 }
 
-// Labels after the merges: every vertex takes its label's root. Merges that
-// meet deletes (this batch's, or deleted forest edges awaiting a warm start)
-// clear the labels instead.
+// Labels after the merges: every vertex takes its label's root. A batch
+// that merged and deleted clears the labels instead.
 __global__ void k_incr_finish(uint32_t* label, uint32_t* ipar, uint32_t V, uint32_t* gc) {
-  if (!ld_cg(&gc[GC_LABELS_VALID])) return;
-  if (ld_cg(&gc[GC_INC_MERGES]) && (ld_cg(&gc[GC_BATCH_DEL]) || ld_cg(&gc[GC_WARM]))) {
+  if (!ld_cg(&gc[GC_LABELS_VALID]) || !ld_cg(&gc[GC_BATCH_MERGE])) return;
+  if (ld_cg(&gc[GC_BATCH_DEL])) {
     if (blockIdx.x == 0 && threadIdx.x == 0) gc[GC_LABELS_VALID] = 0;
     return;
   }
-  if (!ld_cg(&gc[GC_INC_MERGES])) return;  // nothing merged since the recovery
   for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < V; w += gridDim.x * blockDim.x)
     label[w] = inc_find(ipar, label[w], V);
 }
@@ -226,9 +274,22 @@ __global__ void k_incr_finish(uint32_t* label, uint32_t* ipar, uint32_t V, uint3
 cudaError_t launch_incremental(cupc_graph* g, const uint32_t* edges, const int8_t* ops, size_t n, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
   cudaError_t e = cudaMemsetAsync(g->gc + GC_BATCH_DEL, 0, sizeof(uint32_t), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(g->gc + GC_BATCH_MERGE, 0, sizeof(uint32_t), s);
   if (e != cudaSuccess) return e;
+  IncArgs a;
+  a.label = g->label;
+  a.ipar = g->ipar;
+  a.forest_sorted = g->forest_sorted;
+  a.fdead = g->fdead;
+  a.fadd = g->fadd;
+  a.fadd_dead = g->fadd_dead;
+  a.ftab = (unsigned long long*)g->ftab;
+  a.ftab_pos = g->ftab_pos;
+  a.ftab_bits = g->ftab_bits;
+  a.V = g->V;
+  a.gc = g->gc;
   const int grid = (int)std::min<size_t>((n + 255) / 256, (size_t)g->sms * 8);
-  k_incr<<<grid, 256, 0, s>>>(edges, ops, n, g->V, g->label, g->ipar, g->forest_sorted, g->fdead, g->gc);
+  k_incr<<<grid, 256, 0, s>>>(edges, ops, n, a);
   k_incr_finish<<<(int)std::min<size_t>((g->V + 255) / 256, (size_t)g->sms * 4), 256, 0, s>>>(g->label, g->ipar,
                                                                                                 g->V, g->gc);
   return cudaGetLastError();

@@ -131,3 +131,89 @@ def test_warm_start_after_forest_edge_deletes():
     assert np.array_equal(dev.labels(), ref.labels())
     assert len(np.unique(ref.labels())) > 1  # the graph did fall apart
     assert_same_recovery(dev, ref)
+
+
+def test_fixed_forest_stream_keeps_the_labels():
+    # the forest goes in first (one recovery, then merges recorded as forest
+    # edges), then every other edge is inserted and deleted in delete-only
+    # batches: no delete hits the forest, so no further recovery runs, and
+    # every answer equals the oracle's full recovery
+    from paper_2509_14433_gb300 import cupc as C
+    from tests.test_gpu_parity import assert_same_recovery
+    V, seed = 700, 51
+    E, ops, nf = WL.fixed_forest_stream(V, 0.05, seed, cycles=1)
+    dev, ref = _dev(V, seed), O.Graph(V, seed)
+    assert C.cupc_set_incremental(dev.h, 1, None) == 0
+    g = WL.rng(seed)
+    cuts = [0, nf // 3, nf] + list(range(nf + 400, len(E), 400)) + [len(E)]
+    for a, b in zip(cuts[:-1], cuts[1:]):
+        assert dev.update(E[a:b], ops[a:b]) == 0 and ref.update(E[a:b], ops[a:b]) == O.OK
+        pairs = WL.uniform_pairs(V, 300, g, distinct=False)
+        s1, a1 = dev.query(pairs)
+        s2, a2 = ref.query(pairs)
+        assert s1 == s2 == 0 and np.array_equal(a1, a2), a
+    assert dev.stats()["recoveries"] == 1
+    assert np.array_equal(dev.labels(), ref.labels())
+    assert_same_recovery(dev, ref)
+
+
+def test_deleting_merge_edges_recovers_warm():
+    # inserts that join components become forest edges; deleting them (and
+    # recovered forest edges) in a delete-only batch splits the components
+    # again: the next query starts from the remaining fragments
+    from paper_2509_14433_gb300 import cupc as C
+    V, seed = 800, 61
+    g = WL.rng(seed)
+    dev, ref = _dev(V, seed), O.Graph(V, seed)
+    assert C.cupc_set_incremental(dev.h, 1, None) == 0
+    E0 = WL.er_edges(V, 0.002, seed)  # sparse: many components
+    present = set(int(a) * V + int(b) for a, b in E0)
+    assert dev.update(E0) == 0 and ref.update(E0) == O.OK
+    pairs = WL.uniform_pairs(V, 500, g, distinct=False)
+    assert np.array_equal(dev.query(pairs)[1], ref.query(pairs)[1])
+    n0 = dev.stats()["recoveries"]
+    for k in range(3):
+        B = _absent_pairs(V, 150, present, g)
+        present.update(int(a) * V + int(b) for a, b in B)
+        assert dev.update(B) == 0 and ref.update(B) == O.OK  # insert-only: merges, no recovery
+        assert np.array_equal(dev.query(pairs)[1], ref.query(pairs)[1])
+        assert dev.stats()["recoveries"] == n0
+        # delete-only: half of the bridges just added plus some old edges
+        D = np.concatenate([B[: len(B) // 2], np.array([divmod(x, V) for x in
+                                                       sorted(present)[:: max(1, len(present) // 40)]], np.uint32)])
+        D = np.unique(D, axis=0)
+        present.difference_update(int(a) * V + int(b) for a, b in D)
+        o = -np.ones(len(D), np.int8)
+        assert dev.update(D, o) == 0 and ref.update(D, o) == O.OK
+        s1, a1 = dev.query(pairs)
+        s2, a2 = ref.query(pairs)
+        assert s1 == s2 == 0 and np.array_equal(a1, a2), k
+        assert dev.stats()["recoveries"] == n0 + 1
+        assert dev.round_log()[0][0] < V  # warm: round 0 starts from fragments
+        n0 += 1
+    assert np.array_equal(dev.labels(), ref.labels())
+
+
+def test_batcher_updates_drop_incremental_labels():
+    from paper_2509_14433_gb300 import cupc as C
+    V, seed = 500, 71
+    dev, ref = _dev(V, seed), O.Graph(V, seed)
+    assert C.cupc_set_incremental(dev.h, 1, None) == 0
+    E0 = WL.er_edges(V, 0.002, seed)
+    assert dev.update(E0) == 0 and ref.update(E0) == O.OK
+    pairs = WL.uniform_pairs(V, 400, WL.rng(seed), distinct=False)
+    assert np.array_equal(dev.query(pairs)[1], ref.query(pairs)[1])
+    st, b = C.cupc_batcher_create(4, True)
+    assert st == 0
+    try:
+        present = set(int(a) * V + int(x) for a, x in E0)
+        B = _absent_pairs(V, 300, present, WL.rng(seed + 1))
+        e = torch.from_numpy(np.ascontiguousarray(B).reshape(-1)).cuda()
+        o = torch.ones(len(B), dtype=torch.int8, device="cuda")
+        assert C.cupc_batcher_update(b, [dev.h], [e], [o], [len(B)]) == 0
+        torch.cuda.synchronize()
+        ref.update(B)
+        assert np.array_equal(dev.query(pairs)[1], ref.query(pairs)[1])
+        assert np.array_equal(dev.labels(), ref.labels())
+    finally:
+        C.cupc_batcher_destroy(b)
