@@ -63,6 +63,7 @@ def _load():
         "orc_stats": (None, [P, P]),
         "orc_round_log": (None, [P, P, P, P]),
         "orc_export": (None, [P, P]),
+        "orc_import": (None, [P, P]),
         "orc_sketch_sum": (None, [P, P, sz, u32, P]),
         "orc_sample": (ctypes.c_int, [P, P, u32, P]),
         "orc_vertex_sketch": (None, [u32, u64, u32, u32, u32, u32, P, sz, P]),
@@ -183,6 +184,12 @@ class Graph:
         out = np.zeros((self.L, self.V, self.W, 2), dtype=np.uint64)
         _load().orc_export(self._h, _ptr(out))
         return out
+
+    def import_(self, sk: np.ndarray) -> None:
+        """Overwrite every sketch word from a [L][V][W][2] u64 array."""
+        a = np.ascontiguousarray(sk, dtype=np.uint64)
+        assert a.shape == (self.L, self.V, self.W, 2)
+        _load().orc_import(self._h, _ptr(a))
 
     def sketch_sum(self, verts, r: int) -> np.ndarray:
         v = np.ascontiguousarray(np.asarray(verts, dtype=np.uint32))

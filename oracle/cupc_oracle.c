@@ -392,6 +392,21 @@ void orc_export(const orc_graph* g, uint64_t* dst) {
     }
 }
 
+/* The inverse of orc_export: every sketch word from src (same layout). The
+ * sketches are the whole state, so the next query recovers from them. */
+void orc_import(orc_graph* g, const uint64_t* src) {
+  for (uint32_t r = 0; r < g->L; r++)
+    for (uint32_t w = 0; w < g->V; w++) {
+      orc_bucket* x = vertex_layer(g, w, r);
+      const uint64_t* in = src + 2 * (((size_t)r * g->V + w) * g->W);
+      for (uint32_t j = 0; j < g->W; j++) {
+        x[j].alpha = in[2 * j];
+        x[j].gamma = in[2 * j + 1];
+      }
+    }
+  g->dirty = 1;
+}
+
 void orc_sketch_sum(const orc_graph* g, const uint32_t* verts, size_t n, uint32_t r, uint64_t* out) {
   memset(out, 0, sizeof(uint64_t) * 2 * g->W);
   for (size_t i = 0; i < n; i++) {

@@ -49,7 +49,11 @@
  *                              cut is empty, scan-order special cases
  *   orc_recover / query ...... BFS / union-find on exhaustive and random
  *                              small graphs; forest properties; graphs that
- *                              are forests recover themselves
+ *                              are forests recover themselves; planted
+ *                              sketches traced by hand: a checksum-valid
+ *                              sample that does not cross the cut is
+ *                              counted and not hooked, and a ZERO component
+ *                              that absorbs another is sampled again
  */
 #ifndef CUPC_ORACLE_H
 #define CUPC_ORACLE_H
@@ -105,6 +109,9 @@ void orc_round_log(const orc_graph* g, uint32_t* live, uint32_t* ncand, uint64_t
 
 /* Export all sketches as [layer r][vertex w][bucket j] x {alpha, gamma}. */
 void orc_export(const orc_graph* g, uint64_t* dst);
+/* Overwrite every sketch word (orc_export's layout); the next query
+ * recovers from them. Lets tests plant sketch contents no stream makes. */
+void orc_import(orc_graph* g, const uint64_t* src);
 /* Layer-r buckets of the sum of the sketches of vertices verts[0..n). */
 void orc_sketch_sum(const orc_graph* g, const uint32_t* verts, size_t n, uint32_t r, uint64_t* out);
 /* Sample a W-bucket layer-r sketch; returns ORC_ZERO/GOOD/FAIL. */

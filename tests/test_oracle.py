@@ -366,3 +366,58 @@ def test_too_few_rounds_reports_incomplete():
     assert not g.stats()["complete"]
     check_forest_partial = len(f) < V - 1
     assert check_forest_partial
+
+
+def _sketch_of_one_edge(V, seed, u, v):
+    g = O.Graph(V, seed)
+    assert g.update(np.array([[u, v]], np.uint32)) == O.OK
+    sk = g.export()
+    g.close()
+    return sk
+
+
+def test_checksum_valid_sample_outside_the_cut_is_not_hooked():
+    # Planted by hand (rule: a GOOD sample whose edge does not have exactly
+    # one endpoint in the component is a false positive, counted and treated
+    # as FAIL). Vertex 2 carries, in layer 0 only, the sketch words that edge
+    # (4,5) gives vertex 4; every other word is zero. Round 0: eight live
+    # components, vertex 2 samples edge (4,5), which crosses neither of its
+    # sides: one false positive, no candidate, no merge; the seven others are
+    # ZERO. Round 1: only vertex 2 is live, its layer 1 is zero: complete.
+    V, seed = 8, 3
+    one = _sketch_of_one_edge(V, seed, 4, 5)
+    sk = np.zeros_like(one)
+    sk[0, 2] = one[0, 4]
+    g = O.Graph(V, seed)
+    g.import_(sk)
+    st, f = g.spanning_forest()
+    assert st == O.OK and len(f) == 0
+    assert g.labels().tolist() == list(range(V))
+    s = g.stats()
+    assert s["false_pos"] == 1 and s["fail"] == 0 and s["rounds"] == 2 and s["complete"]
+    assert [live for live, _ in g.round_log()] == [8, 1]
+    assert all(len(ids) == 0 for _, ids in g.round_log())
+
+
+def test_zero_component_that_absorbs_another_is_sampled_again():
+    # Planted by hand (rule: a ZERO component is final until it changes).
+    # Edge (0,1) with vertex 0's words cleared: in round 0 vertex 0 is ZERO
+    # (final), vertex 1 samples edge (0,1) = id 1, which crosses its cut, so
+    # {0,1} forms with label 0 and edge 1 in the forest. The merged component
+    # changed, so it is live again in every later round, where its sketch
+    # (vertex 1's words) yields edge 1 with both endpoints inside: a false
+    # positive per round until the layers run out: INCOMPLETE.
+    V, seed = 8, 5
+    sk = _sketch_of_one_edge(V, seed, 0, 1)
+    sk[:, 0] = 0
+    g = O.Graph(V, seed)
+    L = g.L
+    g.import_(sk)
+    st, f = g.spanning_forest()
+    assert st == O.EINCOMPLETE and f.tolist() == [1]
+    assert g.labels().tolist() == [0, 0] + list(range(2, V))
+    s = g.stats()
+    assert s["rounds"] == L and not s["complete"] and s["false_pos"] == L - 1
+    log = g.round_log()
+    assert [live for live, _ in log] == [V] + [1] * (L - 1)
+    assert log[0][1].tolist() == [1] and all(len(ids) == 0 for _, ids in log[1:])
