@@ -151,6 +151,12 @@ cupc_status cupc_sync(cupc_graph* g, cupc_stream stream);
  * bytes must equal L*V*W*16. Synchronises `stream`. For parity checks and
  * checkpoints (the sketches are the whole state: import restores it). */
 cupc_status cupc_export_sketches(cupc_graph* g, void* dst, size_t bytes, cupc_stream stream);
+/* Overwrite all sketches from src (host or device, the export layout); the
+ * next query recovers from them. Imported words need not come from a
+ * stream, so until the next cupc_reset a recovery no longer assumes that
+ * the XOR of all vertex sketches of a layer is zero (it samples the last
+ * live component instead of taking it as ZERO); results stay those of the
+ * recovery rules on whatever words were imported. Synchronises `stream`. */
 cupc_status cupc_import_sketches(cupc_graph* g, const void* src, size_t bytes, cupc_stream stream);
 
 /* Statistics of the last recovery, host array of 8 u64:

@@ -271,6 +271,7 @@ cupc_status cupc_reset(cupc_graph* g, cupc_stream stream) {
   if (!g) return CUPC_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
   CUPC_TRY(cudaMemsetAsync(g->sketch, 0, (size_t)g->L * g->V * g->W * sizeof(ulonglong2), s));
+  g->imported = false;
   return mark_updated(g, s, false);
 }
 
@@ -458,6 +459,7 @@ cupc_status cupc_import_sketches(cupc_graph* g, const void* src, size_t bytes, c
   if (bytes != want) return CUPC_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
   CUPC_TRY(cudaMemcpyAsync(g->sketch, src, want, cudaMemcpyDefault, s));
+  g->imported = true;
   const cupc_status st = mark_updated(g, s, false);
   if (st != CUPC_OK) return st;
   CUPC_TRY(cudaStreamSynchronize(s));

@@ -137,6 +137,8 @@ struct cupc_graph {
   bool dirty;
   bool inc;           // incremental labels (cupc_set_incremental)
   bool forest_stale;  // an update since the last full recovery
+  bool imported;      // words from cupc_import_sketches since the last reset:
+                      // the XOR of all vertex sketches need not be zero
   int device, sms;
   int apply_threads, apply_smem, apply_grid;
   uint32_t item_records, apply_cps;  // tunables: records per work item, CTAs per SM (0 = max)

@@ -50,6 +50,7 @@ struct RecArgs {
   unsigned long long* ftab;  // 2^ftab_bits: the ids of fadd (cleared here)
   uint32_t ftab_bits;
   uint32_t inc, force;  // incremental mode; run even if the labels are valid
+  uint32_t sum_zero;    // the XOR of all vertex sketches of a layer is zero (no import since reset)
   uint32_t* gc;
 };
 
@@ -483,7 +484,8 @@ __global__ void __launch_bounds__(kRecThreads, 2) k_recover(RecArgs a) {
     // vertex sketches of a layer is zero (each edge enters both endpoints),
     // so the live one's merged sketch is zero too and it samples ZERO. Log
     // the round as sampled (one live component, no candidate) and stop.
-    if (multi && ld_cg(&gc[GC_NLIVE]) == 1) {
+    // Imported words need not come from a stream: then the round is run.
+    if (multi && a.sum_zero && ld_cg(&gc[GC_NLIVE]) == 1) {
       if (gtid == 0) {
         a.log_live[r] = 1;
         gc[GC_ROUNDS] = r + 1;
@@ -918,6 +920,7 @@ cudaError_t launch_recover(cupc_graph* g, cudaStream_t s, bool force) {
   a.ftab_bits = g->ftab_bits;
   a.inc = g->inc ? 1u : 0u;
   a.force = force ? 1u : 0u;
+  a.sum_zero = g->imported ? 0u : 1u;
   a.gc = g->gc;
   cudaError_t e = cudaMemsetAsync(g->gc + GC_BAR_COUNT, 0, sizeof(uint32_t), s);
   if (e != cudaSuccess) return e;
