@@ -87,6 +87,13 @@ def expected_touched_buckets(counts, L, C, D):
     return float(L * (mult * (1.0 + C * per_col)).sum())
 
 
+def dense_sweep_bytes(counts, L, W):
+    """Bytes a dense sweep of the batch would move: read and write back the
+    whole sketch (L layers x W buckets x 16 B) of every vertex the batch
+    touches, against the distinct buckets k_apply touches."""
+    return float(2 * 16 * L * W * np.count_nonzero(counts))
+
+
 def apply_source_digest():
     """md5 over the source k_apply compiles from: the shared device header
     (update_dev.cuh), the kernel's own text in update.cu, and the device
@@ -343,6 +350,7 @@ def run_gpu(args):
         counts_per_batch.append(np.bincount(D[i:i + BATCH].reshape(-1), minlength=V_DENSE))
     touched = [expected_touched_buckets(c, L, Cc, Dd) for c in counts_per_batch]
     apply_bytes_per_launch = 32.0 * float(np.mean(touched))
+    sweep_bytes_per_launch = float(np.mean([dense_sweep_bytes(c, L, W) for c in counts_per_batch]))
     apply_launches = int(nl_prof[2])
     apply_ms = ms_prof[2] / max(1, apply_launches)
     peaks = {}
@@ -376,6 +384,7 @@ def run_gpu(args):
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                              "frac": achieved / peak, "traffic": traffic,
                              "kernel": "k_apply", "algorithmic_bytes_per_launch": apply_bytes_per_launch,
+                             "dense_sweep_bytes_per_launch": sweep_bytes_per_launch,
                              "edges_per_launch": BATCH, "avg_launch_ms": apply_ms,
                              "apply_setting": apply_setting,
                              "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst copy)" if peaks else "fallback"},
