@@ -421,3 +421,15 @@ def test_zero_component_that_absorbs_another_is_sampled_again():
     log = g.round_log()
     assert [live for live, _ in log] == [V] + [1] * (L - 1)
     assert log[0][1].tolist() == [1] and all(len(ids) == 0 for _, ids in log[1:])
+
+
+def test_import_restores_an_exported_state():
+    V, seed = 40, 9
+    E = WL.er_edges(V, 0.1, seed)
+    a, b = O.Graph(V, seed), O.Graph(V, seed)
+    assert a.update(E) == O.OK
+    b.import_(a.export())
+    assert np.array_equal(b.export(), a.export())
+    pairs = WL.uniform_pairs(V, 200, WL.rng(seed), distinct=False)
+    assert np.array_equal(b.query(pairs)[1], a.query(pairs)[1])
+    assert np.array_equal(b.spanning_forest()[1], a.spanning_forest()[1])

@@ -90,3 +90,23 @@ def test_fixed_forest_stream_keeps_a_spanning_forest():
     for k in range(4):
         seg = slice(nf + k * rest, nf + (k + 1) * rest)
         assert np.all(ops[seg] == (1 if k % 2 == 0 else -1))
+
+
+def test_serving_streams_are_valid_per_graph():
+    streams = WL.serving_streams(n_graphs=4, v_exp=(6.0, 8.0), upd_range=(3000, 9000),
+                                 batch_range=(50, 800), rho=2000, q_size=10, seed=3)
+    for V, _, steps, done in streams:
+        ups = [(st[1], st[2]) for st in steps if st[0] == "update"]
+        assert sum(len(o) for _, o in ups) == done
+        _replay(ups, V)
+        for st in steps:
+            if st[0] == "query":
+                assert st[1].shape == (10, 2) and int(st[1].max()) < V
+        nq = sum(st[0] == "query" for st in steps)
+        assert nq == done // 2000
+    order = WL.round_robin(streams)
+    assert len(order) == sum(len(s[2]) for s in streams)
+    for i, s in enumerate(streams):  # each graph's steps arrive in its own order
+        mine = [st for j, st in order if j == i]
+        assert len(mine) == len(s[2]) and all(a is b for a, b in zip(mine, s[2]))
+    assert [j for j, _ in order[:len(streams)]] == list(range(len(streams)))
