@@ -201,7 +201,8 @@ cupc_status cupc_profile_read(cupc_graph* g, double* ms, uint64_t* launches, siz
  * host-to-device copy from pinned memory. edges[i]/ops[i] are device
  * pointers with n[i] <= that graph's max_batch entries. Results equal k
  * separate cupc_update_batch calls, including the per-graph sticky error on
- * an invalid batch. Calls on one batcher, and calls touching the same graph,
+ * an invalid batch; a graph with incremental labels drops them instead of
+ * following the batch (its next query recovers in full). Calls on one batcher, and calls touching the same graph,
  * must be ordered on one stream. The batcher owns a small device table, two
  * pinned staging tables and the instantiated graphs. */
 cupc_status cupc_update_batches(cupc_graph* g, const uint32_t* edges, const int8_t* ops, const uint64_t* offsets,
