@@ -105,7 +105,7 @@ def dense_stream(V: int = 16384, p: float = 0.5, batch: int = 1 << 20,
 
 def standard_stream(V: int, p: float, seed: int):
     """The standard stream of a static ER(p) graph, as in the paper's
-    experiments (§6, datasets): insert every edge, then delete every edge,
+    experiments (§5, datasets): insert every edge, then delete every edge,
     each phase in its own seeded random order. Returns edges [2E, 2] uint32
     and ops [2E] int8."""
     e = er_edges(V, p, seed)
@@ -131,7 +131,7 @@ def spanning_forest_edges(V: int, e: np.ndarray, g: np.random.Generator) -> np.n
 
 def fixed_forest_stream(V: int, p: float, seed: int, cycles: int = 1):
     """The fixed forest stream of a static ER(p) graph, as in the paper's
-    experiments (§6 and App. C, datasets): insert the edges of one spanning
+    experiments (§5 and App. C, datasets): insert the edges of one spanning
     forest, then ``cycles`` times insert every other edge and delete them
     all again, each pass in a fresh seeded random order. The forest is never
     deleted, so most updates are non-tree updates. Returns edges [n, 2]
