@@ -50,7 +50,8 @@ def _load():
         "orc_mix64": (u64, [u64]),
         "orc_keys": (None, [u64, P, sz]),
         "orc_params": (None, [u32, P, P, P]),
-        "orc_depth": (u32, [u64, u32]),
+        "orc_hash_bits": (u32, [u32]),
+        "orc_mas_depth": (u32, [u64, u64, u64, u64, u32, u32, u64]),
         "orc_create": (P, [u32, u64, u32, u32, u32]),
         "orc_destroy": (None, [P]),
         "orc_get_params": (None, [P, P]),
@@ -97,8 +98,13 @@ def params(V: int, L: int = 0, C: int = 0, D: int = 0):
     return L, C, D, 1 + C * D
 
 
-def depth(h: int, D: int) -> int:
-    return int(_load().orc_depth(h & (2**64 - 1), D))
+def hash_bits(V: int) -> int:
+    return int(_load().orc_hash_bits(V))
+
+
+def mas_depth(a: int, b: int, a2: int, b2: int, ell: int, D: int, x: int) -> int:
+    m = 2**64 - 1
+    return int(_load().orc_mas_depth(a & m, b & m, a2 & m, b2 & m, ell, D, x & m))
 
 
 def vertex_sketch(V: int, seed: int, w: int, nbrs, L=0, C=0, D=0) -> np.ndarray:

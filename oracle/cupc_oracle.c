@@ -19,7 +19,8 @@ typedef struct {
 struct orc_graph {
   uint32_t V, L, C, D, W;
   uint64_t seed;
-  uint64_t* keys;      /* [L][C+1] */
+  uint32_t ell;        /* output bits of one multiply-add-shift stage */
+  uint64_t* keys;      /* key_count(L, C) words of the SplitMix64 stream */
   orc_bucket* sketch;  /* vertex-major: [w][r][j], j = 0 det, 1 + c*D + d */
   uint32_t* label;     /* component label = min vertex id */
   uint64_t* forest;
@@ -63,15 +64,43 @@ void orc_params(uint32_t V, uint32_t* L, uint32_t* C, uint32_t* D) {
   if (*D == 0) *D = 2 * lg;
 }
 
-/* Depth of an index in one column: the number of trailing zero bits of its
- * hash, capped at the last row. P(depth = j) = 2^-(j+1) below the cap, so an
- * update touches one bucket per column (Theorem A.2's O(log 1/delta)). */
-uint32_t orc_depth(uint64_t h, uint32_t D) {
-  uint32_t d = 0;
-  if (h == 0) return D - 1;
-  while ((h & 1) == 0) {
-    h >>= 1;
-    d++;
+/* Number of key words of a graph: the SplitMix64 stream K(0..) laid out as
+ *   K(r*(C+1) + c), c < C ... multiplier a of column c of layer r
+ *   K(r*(C+1) + C) .......... checksum key of layer r
+ *   K(L*(C+1) + 3*(r*C + c) + k), k = 0, 1, 2 ... b, a', b' of column c */
+static size_t key_count(uint32_t L, uint32_t C) { return (size_t)L * (C + 1) + (size_t)3 * L * C; }
+
+/* Output bits of one multiply-add-shift stage for indices below 2^w,
+ * w = 2*ceil(log2 V): Dietzfelbinger's bound w + ell - 1 <= 64. */
+uint32_t orc_hash_bits(uint32_t V) { return 65 - 2 * ceil_log2(V); }
+
+/* Leading zero bits of an ell-bit value h (ell when h = 0). */
+static uint32_t lead_zeros(uint64_t h, uint32_t ell) {
+  uint32_t z = 0;
+  for (int bit = (int)ell - 1; bit >= 0 && ((h >> bit) & 1) == 0; bit--) z++;
+  return z;
+}
+
+/* Depth of index x in one column (Theorem A.1 asks only for 2-wise
+ * independent hash functions; Theorem A.2's column takes the bucket at the
+ * index's depth). The column hash is multiply-add-shift (Dietzfelbinger,
+ * "Universal hashing and k-wise independent random variables via integer
+ * arithmetic without primes", STACS 1996):
+ *   h(x) = ((a*x + b) mod 2^64) div 2^(64-ell)
+ * with a, b uniform 64-bit words, which is strongly universal (2-wise
+ * independent and uniform) onto ell-bit values when x < 2^(65-ell). Two
+ * independent stages (a, b) and (a', b') give the 2*ell-bit string
+ * h(x) h'(x), and the depth is its number of leading zero bits, capped at
+ * the last row: P(depth >= j) = 2^-j for j <= 2*ell, and the depths of
+ * two different indices are independent. The second stage matters only
+ * when the first is zero, i.e. when ell < D-1 (V > 2^16 at default
+ * parameters). */
+uint32_t orc_mas_depth(uint64_t a, uint64_t b, uint64_t a2, uint64_t b2, uint32_t ell, uint32_t D, uint64_t x) {
+  uint64_t h = (a * x + b) >> (64 - ell);
+  uint32_t d = lead_zeros(h, ell);
+  if (d == ell) {
+    uint64_t h2 = (a2 * x + b2) >> (64 - ell);
+    d += lead_zeros(h2, ell);
   }
   return d < D - 1 ? d : D - 1;
 }
@@ -79,6 +108,11 @@ uint32_t orc_depth(uint64_t h, uint32_t D) {
 static uint64_t key_of(const orc_graph* g, uint32_t r, uint32_t c) { return g->keys[(size_t)r * (g->C + 1) + c]; }
 
 static uint64_t checksum(const orc_graph* g, uint32_t r, uint64_t idx) { return orc_mix64(idx ^ key_of(g, r, g->C)); }
+
+static uint32_t column_depth(const orc_graph* g, uint32_t r, uint32_t c, uint64_t idx) {
+  const uint64_t* k = g->keys + (size_t)g->L * (g->C + 1) + (size_t)3 * (r * g->C + c);
+  return orc_mas_depth(key_of(g, r, c), k[0], k[1], k[2], g->ell, g->D, idx);
+}
 
 static orc_bucket* vertex_layer(const orc_graph* g, uint32_t w, uint32_t r) {
   return g->sketch + ((size_t)w * g->L + r) * g->W;
@@ -95,7 +129,8 @@ orc_graph* orc_create(uint32_t V, uint64_t seed, uint32_t L, uint32_t C, uint32_
   g->D = D;
   g->W = 1 + C * D;
   g->seed = seed;
-  g->keys = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)L * (C + 1));
+  g->ell = orc_hash_bits(V);
+  g->keys = (uint64_t*)malloc(sizeof(uint64_t) * key_count(L, C));
   g->sketch = (orc_bucket*)calloc((size_t)V * L * g->W, sizeof(orc_bucket));
   g->label = (uint32_t*)malloc(sizeof(uint32_t) * V);
   g->forest = (uint64_t*)malloc(sizeof(uint64_t) * V);
@@ -106,7 +141,7 @@ orc_graph* orc_create(uint32_t V, uint64_t seed, uint32_t L, uint32_t C, uint32_
     orc_destroy(g);
     return NULL;
   }
-  orc_keys(seed, g->keys, (size_t)L * (C + 1));
+  orc_keys(seed, g->keys, key_count(L, C));
   for (uint32_t w = 0; w < V; w++) g->label[w] = w;
   g->dirty = 0; /* empty graph: every vertex alone, recovery already exact */
   g->complete = 1;
@@ -140,8 +175,7 @@ static void sketch_layer_update(const orc_graph* g, orc_bucket* layer, uint32_t 
   layer[0].alpha ^= idx;
   layer[0].gamma ^= gam;
   for (uint32_t c = 0; c < g->C; c++) {
-    uint32_t d = orc_depth(orc_mix64(idx ^ key_of(g, r, c)), g->D);
-    orc_bucket* b = &layer[1 + c * g->D + d];
+    orc_bucket* b = &layer[1 + c * g->D + column_depth(g, r, c, idx)];
     b->alpha ^= idx;
     b->gamma ^= gam;
   }
@@ -428,8 +462,9 @@ void orc_vertex_sketch(uint32_t V, uint64_t seed, uint32_t L, uint32_t C, uint32
   tmp.C = C;
   tmp.D = D;
   tmp.W = 1 + C * D;
-  tmp.keys = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)L * (C + 1));
-  orc_keys(seed, tmp.keys, (size_t)L * (C + 1));
+  tmp.ell = orc_hash_bits(V);
+  tmp.keys = (uint64_t*)malloc(sizeof(uint64_t) * key_count(L, C));
+  orc_keys(seed, tmp.keys, key_count(L, C));
   memset(out, 0, sizeof(uint64_t) * 2 * (size_t)L * tmp.W);
   for (size_t i = 0; i < k; i++) {
     uint32_t a = w < nbrs[i] ? w : nbrs[i], b = w < nbrs[i] ? nbrs[i] : w;

@@ -25,12 +25,16 @@
  *     columns C = 7; a layer is 1 deterministic bucket + C*D column buckets;
  *   - a bucket is {alpha = XOR of idx, gamma = XOR of G(idx)}, 2 x u64;
  *   - mix() is the SplitMix64 output finalizer (Steele, Lea, Flood,
- *     OOPSLA 2014); key j = mix(seed + phi*(j+1)), phi = 0x9E3779B97F4A7C15,
- *     i.e. the SplitMix64 stream seeded with `seed`; key index
- *     j = r*(C+1) + c, c = C being the checksum key of layer r;
- *   - column hash h = mix(idx ^ key[r][c]); depth d = min(ctz(h), D-1),
- *     ctz(0) taken as D-1;
- *   - checksum G_r(idx) = mix(idx ^ key[r][C]);
+ *     OOPSLA 2014); key K(j) = mix(seed + phi*(j+1)), phi =
+ *     0x9E3779B97F4A7C15, i.e. the SplitMix64 stream seeded with `seed`;
+ *   - column hash (Theorem A.1 needs 2-wise independence): two stages of
+ *     multiply-add-shift (Dietzfelbinger, STACS 1996),
+ *     h(x) = ((a*x + b) mod 2^64) div 2^(64-ell), ell = 65 - 2*lg, strongly
+ *     universal onto ell bits for x < 2^(2*lg); column c of layer r uses
+ *     a = K(r*(C+1) + c) and b, a', b' = K(L*(C+1) + 3*(r*C + c) + 0, 1, 2);
+ *     depth d = min(leading zeros of the 2*ell-bit string h(x) h'(x), D-1)
+ *     (h' is read only when h(x) = 0);
+ *   - checksum G_r(idx) = mix(idx ^ K(r*(C+1) + C));
  *   - a bucket is good iff alpha != 0, G_r(alpha) == gamma and alpha decodes
  *     to u < v < V;
  *   - sample: det zero -> ZERO; det good -> det; else first good bucket in
@@ -42,7 +46,11 @@
  *
  * Parity pins (what checks this code against something other than itself):
  *   orc_mix64 / keys ......... published SplitMix64 test vectors
- *   orc_depth ................ special cases + geometric depth law
+ *   orc_mas_depth ............ closed forms for chosen keys (powers of two,
+ *                              zero multiplier, wrap-around, second stage);
+ *                              over random keys: the geometric depth law
+ *                              and pairwise independence of two indices
+ *                              (Theorem A.1's requirement)
  *   updates .................. linearity, insert/delete cancellation,
  *                              all-vertex XOR = 0, single-edge recovery
  *   orc_sample ............... cut property on random subsets, ZERO iff the
@@ -81,7 +89,12 @@ uint64_t orc_mix64(uint64_t z);
 void orc_keys(uint64_t seed, uint64_t* out, size_t n);
 /* Parameter derivation; a non-zero input overrides the default. */
 void orc_params(uint32_t V, uint32_t* L, uint32_t* C, uint32_t* D);
-uint32_t orc_depth(uint64_t h, uint32_t D);
+/* Output bits ell of one multiply-add-shift stage for graphs of V vertices. */
+uint32_t orc_hash_bits(uint32_t V);
+/* Depth of index x in a column with keys (a, b, a2, b2): the leading zero
+ * bits of the 2*ell-bit string ((a*x+b) mod 2^64) >> (64-ell) followed by
+ * ((a2*x+b2) mod 2^64) >> (64-ell), capped at D-1. */
+uint32_t orc_mas_depth(uint64_t a, uint64_t b, uint64_t a2, uint64_t b2, uint32_t ell, uint32_t D, uint64_t x);
 
 orc_graph* orc_create(uint32_t V, uint64_t seed, uint32_t L, uint32_t C, uint32_t D);
 void orc_destroy(orc_graph* g);

@@ -45,30 +45,131 @@ def test_params_closed_form():
     assert O.params(1024, 3, 2, 5) == (3, 2, 5, 11)
 
 
-def test_depth_special_cases():
-    D = 20
-    assert O.depth(1, D) == 0
-    assert O.depth(0xFFFF, D) == 0
-    assert O.depth(2, D) == 1
-    assert O.depth(12, D) == 2
-    for k in range(64):
-        assert O.depth(1 << k, D) == min(k, D - 1)
-    assert O.depth(0, D) == D - 1
-    assert O.depth(1 << 63, 34) == 33
+def test_hash_bits_closed_form():
+    # ell = 65 - w, w = 2 ceil(log2 V) bits of an edge index u*V + v < V^2
+    # (Dietzfelbinger's bound w + ell - 1 <= 64 for 64-bit words)
+    assert O.hash_bits(1024) == 45
+    assert O.hash_bits(1000) == 45
+    assert O.hash_bits(16384) == 37
+    assert O.hash_bits(65536) == 33
+    assert O.hash_bits(65537) == 31
+    assert O.hash_bits(131072) == 31
+    assert O.hash_bits(2) == 63
+    for V in (3, 1024, 65536, 131072, 1 << 21):
+        lg = int(np.ceil(np.log2(V)))
+        assert (V - 1) * V + V - 1 < 2 ** (2 * lg) and 2 * lg + O.hash_bits(V) - 1 == 64
 
 
-def test_depth_law_is_geometric():
-    # P(depth = j) = 2^-(j+1): each index lands in one bucket per column and
-    # half of the mass sits in row 0 (Theorem A.2's one-bucket update).
-    n = 1 << 17
-    key = int(O.keys(7, 1)[0])
-    rng = np.random.default_rng(3)
-    idx = rng.integers(1, 2**40, size=n, dtype=np.uint64)
-    d = np.array([O.depth(O.mix64(int(x) ^ key), 20) for x in idx])
+def test_mas_depth_closed_forms():
+    # a = 2^(63-j), b = 0, x = 1: a*x + b = 2^(63-j) has j leading zeros
+    for ell in (31, 37, 45):
+        for D in (20, 28, 34):
+            for j in range(ell):
+                assert O.mas_depth(1 << (63 - j), 0, 0, 0, ell, D, 1) == min(j, D - 1)
+    # zero multiplier: the depth is that of b's top ell bits, for every x
+    for x in (0, 1, 12345, 2**40 - 1):
+        assert O.mas_depth(0, 1 << 63, 0, 0, 37, 28, x) == 0
+        assert O.mas_depth(0, 1 << 59, 0, 0, 37, 28, x) == 4
+        assert O.mas_depth(0, (1 << 30) - 1, 0, 0, 37, 28, x) == 27  # below the top 37 bits: capped
+    # x = 0 gives b; wrap-around mod 2^64: 2^63 * 2 = 0
+    assert O.mas_depth(0x123456789, 1 << 60, 0, 0, 37, 28, 0) == 3
+    assert O.mas_depth(1 << 63, 1 << 62, 0, 0, 37, 28, 2) == 1
+    # the product a*x + b carries into the top bits: 3 * 2^61 + 2^61 = 2^63
+    assert O.mas_depth(3 << 61, 1 << 61, 0, 0, 37, 28, 1) == 0
+    # a zero first stage hands over to the second: ell + its leading zeros
+    ell = 31
     for j in range(8):
-        p = 2.0 ** -(j + 1)
-        sd = np.sqrt(n * p * (1 - p))
-        assert abs((d == j).sum() - n * p) < 5 * sd, j
+        assert O.mas_depth(0, 0, 1 << (63 - j), 0, ell, 34, 1) == min(ell + j, 33)
+    assert O.mas_depth(0, 0, 0, 0, ell, 34, 99) == 33
+    # a non-zero first stage ignores the second
+    assert O.mas_depth(1 << 62, 0, 0, 0, ell, 34, 1) == 1
+    # only the top ell bits count: 2^(64-ell-1) is zero in them
+    assert O.mas_depth(1 << (64 - ell - 1), 0, 0, 0, ell, 34, 1) == 33
+    assert O.mas_depth(1 << (64 - ell - 1), 0, 1 << 63, 0, ell, 34, 1) == ell
+
+
+def _random_keys(rng, n):
+    return rng.integers(0, 2**63, size=(n, 4), dtype=np.uint64) * 2 + rng.integers(0, 2, size=(n, 4), dtype=np.uint64)
+
+
+def test_mas_depth_law_over_random_keys_is_geometric():
+    # strong universality makes the ell-bit hash of a fixed index uniform
+    # over the keys, so P(depth = j) = 2^-(j+1) (one bucket per column,
+    # Theorem A.2), for indices whose low bits vary and ones whose do not
+    n = 1 << 15
+    rng = np.random.default_rng(3)
+    for V, x in ((16384, 5), (16384, (1 << 27) + 1), (131072, 7 * 131072 + 9)):
+        ell, D = O.hash_bits(V), 2 * int(np.log2(V))
+        K = _random_keys(rng, n)
+        d = np.array([O.mas_depth(*map(int, k), ell, D, x) for k in K])
+        for j in range(8):
+            p = 2.0 ** -(j + 1)
+            sd = np.sqrt(n * p * (1 - p))
+            assert abs((d == j).sum() - n * p) < 5 * sd, (V, x, j)
+
+
+def test_mas_depths_of_two_indices_are_independent():
+    # Theorem A.1's 2-wise independence: over random keys, the depths of two
+    # different indices are independent. Pairs differ in the low bit only, in
+    # a high bit only, or everywhere; a hash read from the low product bits,
+    # or with a shared key across columns, fails this.
+    n = 1 << 14
+    rng = np.random.default_rng(11)
+    V = 16384
+    ell, D = O.hash_bits(V), 28
+    for x, y in ((6, 7), (5, 5 + (1 << 26)), (123456, 98765432)):
+        K = _random_keys(rng, n)
+        dx = np.array([min(O.mas_depth(*map(int, k), ell, D, x), 2) for k in K])
+        dy = np.array([min(O.mas_depth(*map(int, k), ell, D, y), 2) for k in K])
+        pm = np.array([0.5, 0.25, 0.25])
+        for i in range(3):
+            for j in range(3):
+                p = pm[i] * pm[j]
+                sd = np.sqrt(n * p * (1 - p))
+                assert abs(((dx == i) & (dy == j)).sum() - n * p) < 5 * sd, (x, y, i, j)
+
+
+def test_column_rows_follow_the_key_layout():
+    # column c of layer r takes a = K(r(C+1)+c), (b, a', b') = K(L(C+1) +
+    # 3(rC+c) + 0..2) from the published key stream; the checksum key of
+    # layer r is K(r(C+1)+C)
+    for V, seed in ((37, 5), (3000, 9)):
+        L, C, D, W = O.params(V)
+        K = [int(x) for x in O.keys(seed, L * (C + 1) + 3 * L * C)]
+        ell = O.hash_bits(V)
+        g = O.Graph(V, seed)
+        u, v = 3, 30
+        g.update(np.array([[u, v]], np.uint32))
+        idx = u * V + v
+        ex = g.export()
+        for r in range(L):
+            chk = O.mix64(idx ^ K[r * (C + 1) + C])
+            assert tuple(ex[r, u, 0]) == (idx, chk)
+            for c in range(C):
+                base = L * (C + 1) + 3 * (r * C + c)
+                d = O.mas_depth(K[r * (C + 1) + c], K[base], K[base + 1], K[base + 2], ell, D, idx)
+                assert tuple(ex[r, u, 1 + c * D + d]) == (idx, chk)
+        g.close()
+
+
+def test_vertex_sketch_equals_the_graph_export():
+    # the one-vertex sketch (used to check large graphs vertex by vertex)
+    # equals the full oracle's export for the same edges, whichever endpoint
+    # of each edge the vertex is (neighbours above and below w)
+    rng = np.random.default_rng(8)
+    for V, seed in ((50, 3), (700, 12)):
+        g = O.Graph(V, seed)
+        E = WL.uniform_pairs(V, 4 * V, rng)
+        ids = np.unique(np.minimum(E[:, 0], E[:, 1]).astype(np.int64) * V + np.maximum(E[:, 0], E[:, 1]))
+        E = np.stack([ids // V, ids % V], 1).astype(np.uint32)
+        g.update(E)
+        ex = g.export()
+        for w in (0, 1, V // 2, V - 1):
+            nb = np.concatenate([E[E[:, 0] == w, 1], E[E[:, 1] == w, 0]])
+            if w == V // 2:  # a vertex that is the smaller and the larger endpoint
+                assert (nb > w).any() and (nb < w).any()
+            assert np.array_equal(O.vertex_sketch(V, seed, w, nb), ex[:, w]), (V, w)
+        g.close()
 
 
 # ---- sketch updates: linearity and cancellation (App. A.1.1) ---------------
