@@ -283,6 +283,13 @@ cupc_status cupc_get_params(const cupc_graph* g, uint32_t* out4);
 void cupc_destroy(cupc_graph* g);
 const char* cupc_status_string(cupc_status s);
 
+/* The architecture the library's kernels were built for, as the CUDA
+ * runtime of the current device reports it for the update kernel:
+ * binary (SASS) and PTX versions, major*10 + minor (103 for sm_103a).
+ * Needs a device; returns CUPC_ECUDA when the runtime cannot load the
+ * kernel image for it, CUPC_EINVAL for null outputs. */
+cupc_status cupc_build_info(int* binary_version, int* ptx_version);
+
 /* Self-test of failure detection on the device: every wait a library kernel
  * makes on other CTAs is bounded. This launches `ctas` (2..64) co-resident
  * CTAs that meet at a grid barrier, of which CTA `absent_cta` (-1: none)
@@ -302,20 +309,24 @@ cupc_status cupc_selftest_wait_timeout(uint32_t ctas, uint32_t limit_us, int abs
  * cupc_update_batch, default parameters for V) to a sketch buffer the caller
  * owns, `sketch`, laid out exactly as cupc_export_sketches writes it
  * (L*V*W*16 bytes, device memory, zero = the empty graph), hashed with
- * `seed`. edges/ops must be device pointers. Its scratch is one static
- * device array of fixed size in the library (about 2.6 MB per GPU that loads
- * the library, held until the process exits), so it accepts at most
- * CUPC_STATIC_MAX_V vertices and CUPC_STATIC_MAX_EDGES edges per call and
- * returns CUPC_EINVAL beyond that, before any work. The first call on a
- * device sets up that device (looks up the array's device address and the
- * kernel's launch shape) with the device current; make that first call
- * before any stream capture. Every call on a device shares the one array
+ * `seed`. sketch (16-byte aligned), edges and ops must be device (or
+ * managed) memory: anything else returns CUPC_EINVAL before any launch.
+ * Its scratch is one static device array of CUPC_STATIC_SCRATCH_BYTES
+ * (about 3.5 MB) in the library, held by every GPU that loads the library
+ * until the process exits, so it accepts at most CUPC_STATIC_MAX_V vertices
+ * and CUPC_STATIC_MAX_EDGES edges per call and returns CUPC_EINVAL beyond
+ * that, before any work. The first call on a device sets up that device
+ * (looks up the array's device address and the kernel's launch shape) with
+ * the device current; make that first call before any stream capture. A
+ * set-up that fails returns CUPC_ECUDA and is tried again by the next call.
+ * Every call on a device shares the one array
  * and clears what must start at zero; calls whose work overlaps on the GPU
  * (other streams, other host threads) race on it, so order them. An invalid
  * edge drops the whole batch; status_out (nullable, device or host) receives
  * the error bits of this call (0 = applied, 1 = dropped), stream-ordered. */
 #define CUPC_STATIC_MAX_V 65536u
 #define CUPC_STATIC_MAX_EDGES 65536u
+#define CUPC_STATIC_SCRATCH_BYTES 3494656u
 cupc_status cupc_update_sketch_static(void* sketch, uint32_t V, uint64_t seed, const uint32_t* edges,
                                       const int8_t* ops, size_t n, uint32_t* status_out, cupc_stream stream);
 

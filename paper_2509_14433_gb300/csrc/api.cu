@@ -76,7 +76,7 @@ Layout layout(const Dims& d) {
   const size_t V = d.V, B = d.max_batch;
   const size_t nitems = 4 * B / kMinItemRecords + (V < 2 * B ? V : 2 * B) + 2 * kPlanGridCap + 1;
   l.sketch = take((size_t)d.L * V * d.W * sizeof(ulonglong2));
-  l.keys = take((size_t)d.L * (d.C + 1) * sizeof(uint64_t));
+  l.keys = take(key_words(d.L, d.C) * sizeof(uint64_t));
   l.gc = take(GC_SLOTS * sizeof(uint32_t));
   l.cnt = take(V * 4);
   l.cursor = take(V * 4);

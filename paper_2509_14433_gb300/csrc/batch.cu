@@ -37,7 +37,9 @@ struct alignas(16) InstDesc {
   uint32_t item_base;  // first work item of this graph (set by k_plan_m)
   uint32_t nitems;     // set by k_plan_m
   uint32_t nd;         // direct-path records (set by k_plan_m)
-  uint32_t pad[3];
+  uint32_t ell;        // bits of one column-hash stage
+  uint32_t long_depth; // depths may need the slow path
+  uint32_t pad[1];
 };
 
 struct alignas(16) BatchHead {
@@ -160,11 +162,9 @@ __global__ void k_scatter_m(const BatchHead* __restrict__ h) {
 // Persistent CTAs pull work items of all graphs from one counter. The lane
 // layout follows the graph of the current item (recomputed when it changes);
 // rows stay zero between items, so CTAs move freely between graphs.
-__global__ void k_apply_m(BatchHead* __restrict__ h, uint32_t rmax, uint32_t items_max) {
+__global__ void k_apply_m(BatchHead* __restrict__ h, uint32_t rmax, uint32_t lmax) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  ulonglong2* s_xp = reinterpret_cast<ulonglong2*>(smem_raw);
-  ulonglong2* s_acc = s_xp + items_max;
-  uint32_t* s_w = reinterpret_cast<uint32_t*>(s_acc + (size_t)rmax * blockDim.x);
+  const ApplySmem m = apply_smem(smem_raw, rmax, lmax);
   __shared__ uint32_t s_item;
   const InstDesc* d = descs_of(h);
   const uint32_t k = h->k;
@@ -172,7 +172,7 @@ __global__ void k_apply_m(BatchHead* __restrict__ h, uint32_t rmax, uint32_t ite
   // counter hands out the rest, counting from the grid size
   const uint32_t total = ld_cg(&h->total_items);
   if (blockIdx.x >= total) return;
-  ulonglong2* my_rows = s_acc + threadIdx.x;
+  ulonglong2* my_rows = m.rows + threadIdx.x;
   const uint32_t rs = blockDim.x;
   for (uint32_t r = 0; r < rmax; r++) my_rows[r * rs] = make_ulonglong2(0, 0);
   uint32_t cur = kNoneU32;
@@ -182,20 +182,23 @@ __global__ void k_apply_m(BatchHead* __restrict__ h, uint32_t rmax, uint32_t ite
     const InstDesc& g = d[j];
     if (j != cur) {
       cur = j;
-      l = apply_lane(g.keys, g.L, g.C, g.D, g.P, g.R);
+      l = apply_lane(g.keys, g.L, g.C, g.D, g.P, g.R, g.ell);
+      __syncthreads();  // every thread is done with the previous graph's keys
+      load_kchk(m, g.keys, g.L, g.C);
+      __syncthreads();
     }
     const uint4 item = g.items[it - ld_cg(&g.item_base)];
     if (item.x == kDirectItem) {
-      if (g.D > 32)
-        apply_direct<true>(l, g.sketch, g.V, g.W, g.rec + item.y, g.recw + item.y, item.z - item.y, g.D, s_xp, s_w);
+      if (g.long_depth)
+        apply_direct<true>(l, g.sketch, g.V, g.W, g.rec + item.y, g.recw + item.y, item.z - item.y, g.L, m);
       else
-        apply_direct<false>(l, g.sketch, g.V, g.W, g.rec + item.y, g.recw + item.y, item.z - item.y, g.D, s_xp, s_w);
+        apply_direct<false>(l, g.sketch, g.V, g.W, g.rec + item.y, g.recw + item.y, item.z - item.y, g.L, m);
     } else {
       ulonglong2* gb = g.sketch + ((size_t)l.layer * g.V + item.x) * g.W + l.jbase;
-      if (g.D > 32)
-        apply_item<true>(l, gb, g.rec + item.y, item.z - item.y, item.w != 0, g.D, g.R, s_xp, my_rows, rs);
+      if (g.long_depth)
+        apply_item<true>(l, gb, g.rec + item.y, item.z - item.y, item.w != 0, g.L, g.R, m, my_rows, rs);
       else
-        apply_item<false>(l, gb, g.rec + item.y, item.z - item.y, item.w != 0, g.D, g.R, s_xp, my_rows, rs);
+        apply_item<false>(l, gb, g.rec + item.y, item.z - item.y, item.w != 0, g.L, g.R, m, my_rows, rs);
     }
     // both item paths end with __syncthreads: every thread has read s_item
     if (threadIdx.x == 0) s_item = gridDim.x + atomicAdd(&h->next_item, 1u);
@@ -219,7 +222,7 @@ struct cupc_batcher {
   int cur;
   cudaStream_t cap_stream;
   struct Exec {
-    uint32_t threads, rmax, imax;
+    uint32_t threads, rmax, lmax;
     int apply_grid, apply_smem;
     cudaGraphExec_t exec[2];
   };
@@ -245,21 +248,21 @@ cudaError_t enqueue(cupc_batcher* b, int slot, const cupc_batcher::Exec& x, cuda
   k_count_m<<<grid, 256, 0, s>>>(b->dtab);
   k_plan_m<<<b->max_graphs, 1024, 0, s>>>(b->dtab);
   k_scatter_m<<<grid, 256, 0, s>>>(b->dtab);
-  k_apply_m<<<x.apply_grid, x.threads, x.apply_smem, s>>>(b->dtab, x.rmax, x.imax);
+  k_apply_m<<<x.apply_grid, x.threads, x.apply_smem, s>>>(b->dtab, x.rmax, x.lmax);
   return cudaGetLastError();
 }
 
-cudaError_t get_exec(cupc_batcher* b, uint32_t threads, uint32_t rmax, uint32_t imax, cupc_batcher::Exec** out) {
+cudaError_t get_exec(cupc_batcher* b, uint32_t threads, uint32_t rmax, uint32_t lmax, cupc_batcher::Exec** out) {
   for (auto& x : b->execs)
-    if (x.threads == threads && x.rmax == rmax && x.imax == imax) {
+    if (x.threads == threads && x.rmax == rmax && x.lmax == lmax) {
       *out = &x;
       return cudaSuccess;
     }
   cupc_batcher::Exec x{};
   x.threads = threads;
   x.rmax = rmax;
-  x.imax = imax;
-  x.apply_smem = (int)apply_smem_bytes(imax, rmax, threads);
+  x.lmax = lmax;
+  x.apply_smem = (int)apply_smem_bytes(rmax, threads, lmax);
   cudaFuncAttributes fa;
   cudaError_t e = cudaFuncGetAttributes(&fa, k_apply_m);
   if (e != cudaSuccess) return e;
@@ -338,7 +341,7 @@ cupc_status cupc_batcher_update(cupc_batcher* b, cupc_graph* const* graphs, cons
   memset(h, 0, sizeof(BatchHead) + (size_t)k * sizeof(InstDesc));
   InstDesc* d = reinterpret_cast<InstDesc*>(h + 1);
   uint64_t base = 0;
-  uint32_t threads = 32, rmax = 1, imax = kMinItemRecords;
+  uint32_t threads = 32, rmax = 1, lmax = 1;
   for (uint32_t i = 0; i < k; i++) {
     cupc_graph* g = graphs[i];
     InstDesc& x = d[i];
@@ -362,15 +365,17 @@ cupc_status cupc_batcher_update(cupc_batcher* b, cupc_graph* const* graphs, cons
     x.P = g->P;
     x.R = g->R;
     x.item_records = g->item_records;
+    x.ell = g->ell;
+    x.long_depth = g->long_depth ? 1u : 0u;
     base += n[i];
     if ((uint32_t)g->apply_threads > threads) threads = (uint32_t)g->apply_threads;
     if (g->R > rmax) rmax = g->R;
-    if (g->item_records > imax) imax = g->item_records;
+    if (g->L > lmax) lmax = g->L;
   }
   h->k = k;
   h->total_edges = base;
   cupc_batcher::Exec* x = nullptr;
-  if (get_exec(b, threads, rmax, imax, &x) != cudaSuccess) {
+  if (get_exec(b, threads, rmax, lmax, &x) != cudaSuccess) {
     cudaGetLastError();
     return CUPC_ECUDA;
   }

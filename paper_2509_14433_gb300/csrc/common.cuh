@@ -47,10 +47,25 @@ constexpr uint32_t kPlanSlices = 1024;
 // Most CTAs of the single-graph apply kernel (its direct-path items number
 // at most 2 per CTA + 1 beyond one per 64 direct records).
 constexpr uint32_t kPlanGridCap = 8192;
-// Dynamic shared memory of an apply CTA: staged records {idx, pre(idx)},
-// rows x threads fold rows, and the records' vertices (direct path).
-inline size_t apply_smem_bytes(uint32_t item_records, uint32_t rows, uint32_t threads) {
-  return ((size_t)item_records + (size_t)rows * threads) * 16 + (size_t)item_records * 4;
+// Records an apply CTA stages per pass: idx and the checksums G_r(idx) of
+// every layer of kStage records sit in shared memory.
+constexpr uint32_t kStage = 64;
+// Dynamic shared memory of an apply CTA for graphs of at most L layers:
+// rows x threads fold rows, kStage staged records with their L checksums,
+// the L layer checksum keys and the records' vertices (direct path).
+inline size_t apply_smem_bytes(uint32_t rows, uint32_t threads, uint32_t L) {
+  return (size_t)rows * threads * 16 + (size_t)kStage * 8 * (1 + L) + (size_t)L * 8 + (size_t)kStage * 4;
+}
+// Key words of a graph: L*(C+1) (column multipliers and layer checksum
+// keys) + 3*L*C (the other multiply-add-shift words of every column).
+constexpr size_t key_words(uint32_t L, uint32_t C) { return (size_t)L * (C + 1) + (size_t)3 * L * C; }
+// Output bits of one multiply-add-shift stage for indices below V^2:
+// 65 - 2*ceil(log2 V) (strong universality with 64-bit words).
+inline uint32_t hash_bits(uint32_t V) {
+  uint32_t lg = 0;
+  while (((uint64_t)1 << lg) < (uint64_t)V) lg++;
+  if (lg < 1) lg = 1;
+  return 65 - 2 * lg;
 }
 // Threads of the recovery kernel and members per reduction work item.
 constexpr uint32_t kRecThreads = 256;
@@ -103,13 +118,6 @@ __host__ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
   return z ^ (z >> 31);
 }
 
-// Row of an index in a column: trailing zeros of its hash, capped at D-1.
-__device__ __forceinline__ uint32_t depth_of(uint64_t h, uint32_t D) {
-  int f = __ffsll((long long)h);
-  uint32_t d = f ? (uint32_t)(f - 1) : D - 1;
-  return d < D - 1 ? d : D - 1;
-}
-
 __device__ __forceinline__ uint64_t global_timer_ns() {
   uint64_t t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -129,6 +137,8 @@ __device__ __forceinline__ uint8_t ld_cg(const uint8_t* p) {
 // Host-side state of one graph. Device arrays are carved from one workspace.
 struct cupc_graph {
   uint32_t V, L, C, D, W, P, R;  // P: lanes per layer in the update kernel
+  uint32_t ell;                  // bits of one column-hash stage (hash_bits(V))
+  bool long_depth;               // ell < D-1 or D-1 > 32: depths may need the slow path
   uint64_t seed;
   uint32_t max_batch, max_pairs;
   void* ws;
@@ -151,7 +161,7 @@ struct cupc_graph {
   int rec_grid;
   // sketches and keys
   ulonglong2* sketch;  // L*V*W
-  uint64_t* keys;      // L*(C+1)
+  uint64_t* keys;      // key_words(L, C)
   uint32_t* gc;        // GC_SLOTS device counters
   // update scratch
   uint32_t* cnt;       // V

@@ -16,7 +16,8 @@ namespace {
 
 constexpr uint32_t kMaxV = CUPC_STATIC_MAX_V;
 constexpr uint32_t kMaxEdges = CUPC_STATIC_MAX_EDGES;
-constexpr uint32_t kMaxKeys = 64 * 8;
+// key words of the widest graph: V = kMaxV has L = 18 layers, C = 7 columns
+constexpr uint32_t kMaxKeys = (uint32_t)key_words(18, 7);
 constexpr size_t kAlignS = 256;
 constexpr size_t align_s(size_t x) { return (x + kAlignS - 1) / kAlignS * kAlignS; }
 constexpr size_t kMaxItems =
@@ -31,6 +32,7 @@ constexpr size_t kOffRecw = align_s(kOffRec + 2ull * kMaxEdges * sizeof(uint64_t
 constexpr size_t kOffItems = align_s(kOffRecw + 2ull * kMaxEdges * sizeof(uint32_t));
 constexpr size_t kOffPart = align_s(kOffItems + kMaxItems * sizeof(uint4));
 constexpr size_t kScratchBytes = align_s(kOffPart + kPlanSlices * sizeof(uint4));
+static_assert(kScratchBytes == CUPC_STATIC_SCRATCH_BYTES, "the header states the size of the static scratch");
 
 // Shared by every call on a device, kept between calls.
 static __device__ __align__(256) unsigned char cupc_static_scratch[kScratchBytes];
@@ -63,28 +65,45 @@ void fill_dims(cupc_graph& g, uint32_t V) {
   g.W = 1 + g.C * g.D;
 }
 
+// A set-up that fails is not kept: the next call on that device tries
+// again (a failure can be transient, or the first call may have come during
+// a stream capture).
 cudaError_t device_setup(int dev, DeviceSetup** out) {
   std::lock_guard<std::mutex> lock(g_setup_mutex);
   DeviceSetup& s = g_setup[dev];
   if (!s.done) {
-    s.done = true;
-    s.err = cudaGetSymbolAddress((void**)&s.scratch, cupc_static_scratch);
-    if (s.err == cudaSuccess) s.err = cudaDeviceGetAttribute(&s.sms, cudaDevAttrMultiProcessorCount, dev);
-    if (s.err == cudaSuccess) {
+    cudaError_t err = cudaGetSymbolAddress((void**)&s.scratch, cupc_static_scratch);
+    if (err == cudaSuccess) err = cudaDeviceGetAttribute(&s.sms, cudaDevAttrMultiProcessorCount, dev);
+    if (err == cudaSuccess) {
       // the widest apply launch: V = kMaxV sets the most layers
       cupc_graph g{};
       fill_dims(g, kMaxV);
       g.sms = s.sms;
-      s.err = setup_update(&g);
+      err = setup_update(&g);
       s.apply_threads = g.apply_threads;
       s.apply_smem = g.apply_smem;
       s.apply_grid = g.apply_grid;
       s.P = g.P;
       s.R = g.R;
     }
+    if (err != cudaSuccess) {
+      cudaGetLastError();  // clear it, so that a later call starts clean
+      return err;
+    }
+    s.done = true;
   }
   *out = &s;
-  return s.err;
+  return cudaSuccess;
+}
+
+// Device or managed memory (cudaPointerGetAttributes allocates nothing).
+bool device_memory(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
 }  // namespace
@@ -94,6 +113,11 @@ extern "C" cupc_status cupc_update_sketch_static(void* sketch, uint32_t V, uint6
                                                  cupc_stream stream) {
   if (!sketch || V < 2 || V > kMaxV || n > kMaxEdges) return CUPC_EINVAL;
   if (n > 0 && (!edges || !ops)) return CUPC_EINVAL;
+  // the kernels read and write these directly: a host address here would
+  // fault on the GPU, so it is refused before any launch; the apply kernel
+  // accesses the sketch 16 bytes at a time
+  if (((uintptr_t)sketch & 15) != 0 || !device_memory(sketch)) return CUPC_EINVAL;
+  if (n > 0 && (!device_memory(edges) || !device_memory(ops))) return CUPC_EINVAL;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return CUPC_ECUDA;
   DeviceSetup* ds = nullptr;
@@ -107,9 +131,11 @@ extern "C" cupc_status cupc_update_sketch_static(void* sketch, uint32_t V, uint6
   g.sms = ds->sms;
   g.P = ds->P;
   g.R = g.D < kSmemRows ? g.D : kSmemRows;
+  g.ell = hash_bits(V);
+  g.long_depth = g.ell < g.D - 1 || g.D - 1 > 32;
   g.item_records = kDefaultItemRecords;
   g.apply_threads = (int)(((g.L * g.P) + 31) / 32 * 32);
-  g.apply_smem = (int)apply_smem_bytes(g.item_records, g.R, (uint32_t)g.apply_threads);
+  g.apply_smem = (int)apply_smem_bytes(g.R, (uint32_t)g.apply_threads, g.L);
   // the set-up sized the launch for the widest graph; a narrower one fits
   g.apply_grid = ds->apply_grid;
   g.prof_on = false;

@@ -206,9 +206,19 @@ void admit(cupc_server* s) {
       return;  // wait for memory
     }
     cupc_graph* g = nullptr;
-    if (cupc_init(in.V, in.seed, &p, (char*)s->arena + off, s->upd_stream, &g) != CUPC_OK) {
+    const cupc_status st = cupc_init(in.V, in.seed, &p, (char*)s->arena + off, s->upd_stream, &g);
+    if (st != CUPC_OK) {
+      // the graph cannot be created: finish its queued requests with that
+      // status and refuse later ones, so the graphs behind it still admit
       s->arena_alloc.release(off);
-      return;
+      s->admit_q.pop_front();
+      in.closed = true;
+      while (!in.q.empty()) {
+        finish_ticket(s, in.q.front(), st, Clock::now());
+        in.q.pop_front();
+      }
+      s->cv_done.notify_all();
+      continue;
     }
     in.g = g;
     in.slot = s->free_slots.back();

@@ -14,12 +14,15 @@
 //             16..64 records of vertices with at most 2 (the direct path)
 //   k_scatter endpoint records (the edge index u*V+v) grouped by vertex
 //             (k_scatter_priv with k_count_priv)
-//   k_apply   persistent CTAs, CTA b starting on item b; thread (layer r,
-//             slot s) hashes every record of the item for column s of layer
-//             r (slot C computes the checksum and owns the deterministic
-//             bucket), folds them in shared memory, then read-modify-writes
-//             only the touched buckets of that vertex in HBM with 16-byte
-//             accesses; direct items XOR each bucket straight into HBM.
+//   k_apply   persistent CTAs, CTA b starting on item b; the CTA stages
+//             the item's records 64 at a time with their checksum of every
+//             layer (one SplitMix64 per record and layer), then thread
+//             (layer r, slot s) takes the multiply-add-shift depth of each
+//             record in column s of layer r (slot C owns the deterministic
+//             bucket), folds it into shared-memory rows, and finally
+//             read-modify-writes only the touched buckets of that vertex in
+//             HBM with 16-byte accesses; direct items XOR each bucket
+//             straight into HBM.
 // XOR is associative and commutative, so the result is bit-identical to
 // applying the updates one by one in stream order.
 #include "update_dev.cuh"
@@ -33,8 +36,7 @@ __global__ void k_keys(uint64_t seed, uint64_t* keys, uint32_t n) {
 }
 
 cudaError_t launch_keys(cupc_graph* g, cudaStream_t s) {
-  uint32_t n = g->L * (g->C + 1);
-  k_keys<<<1, 256, 0, s>>>(g->seed, g->keys, n);
+  k_keys<<<1, 256, 0, s>>>(g->seed, g->keys, (uint32_t)key_words(g->L, g->C));
   return cudaGetLastError();
 }
 
@@ -418,15 +420,13 @@ __global__ void k_scatter(const uint32_t* __restrict__ edges, size_t n, uint32_t
 
 // Fold the records of one work item into the sketches of its vertex (see
 // apply_item); persistent CTAs pull work items from a counter.
-template <bool kWide>
+template <bool kLong>
 __global__ void k_apply(ulonglong2* __restrict__ sketch, const uint64_t* __restrict__ keys,
                         const uint64_t* __restrict__ rec, const uint32_t* __restrict__ recw,
                         const uint4* __restrict__ items, uint32_t* gc, uint32_t V, uint32_t L, uint32_t C,
-                        uint32_t D, uint32_t W, uint32_t P, uint32_t R, uint32_t item_records) {
+                        uint32_t D, uint32_t W, uint32_t P, uint32_t R, uint32_t ell) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  ulonglong2* s_xp = reinterpret_cast<ulonglong2*>(smem_raw);  // {idx, pre(idx)}
-  ulonglong2* s_acc = s_xp + item_records;
-  uint32_t* s_w = reinterpret_cast<uint32_t*>(s_acc + (size_t)R * blockDim.x);
+  const ApplySmem m = apply_smem(smem_raw, R, L);
   __shared__ uint32_t s_item;
 
   if (ld_cg(&gc[GC_ERR]) & kErrInval) return;
@@ -436,18 +436,20 @@ __global__ void k_apply(ulonglong2* __restrict__ sketch, const uint64_t* __restr
   // from the counter, which counts from the grid size
   const uint32_t nitems = ld_cg(&gc[GC_NITEMS]);
   if (blockIdx.x >= nitems) return;
-  const ApplyLane l = apply_lane(keys, L, C, D, P, R);
-  ulonglong2* my_rows = s_acc + threadIdx.x;
+  const ApplyLane l = apply_lane(keys, L, C, D, P, R, ell);
+  load_kchk(m, keys, L, C);
+  ulonglong2* my_rows = m.rows + threadIdx.x;
   const uint32_t rs = blockDim.x;
   for (uint32_t d = 0; d < R; d++) my_rows[d * rs] = make_ulonglong2(0, 0);
+  __syncthreads();
 
   for (uint32_t it = blockIdx.x; it < nitems;) {
     const uint4 item = items[it];
     if (item.x == kDirectItem) {
-      apply_direct<kWide>(l, sketch, V, W, rec + item.y, recw + item.y, item.z - item.y, D, s_xp, s_w);
+      apply_direct<kLong>(l, sketch, V, W, rec + item.y, recw + item.y, item.z - item.y, L, m);
     } else {
       ulonglong2* gb = sketch + ((size_t)l.layer * V + item.x) * W + l.jbase;
-      apply_item<kWide>(l, gb, rec + item.y, item.z - item.y, item.w != 0, D, R, s_xp, my_rows, rs);
+      apply_item<kLong>(l, gb, rec + item.y, item.z - item.y, item.w != 0, L, R, m, my_rows, rs);
     }
     // both item paths end with __syncthreads: every thread has read s_item
     if (threadIdx.x == 0) s_item = gridDim.x + atomicAdd(&gc[GC_NEXT_ITEM], 1u);
@@ -481,6 +483,8 @@ cudaError_t setup_update(cupc_graph* g) {
   g->P = 1;
   while (g->P < g->C + 1) g->P <<= 1;
   g->R = g->D < kSmemRows ? g->D : kSmemRows;
+  g->ell = hash_bits(g->V);
+  g->long_depth = g->ell < g->D - 1 || g->D - 1 > 32;
   g->item_records = kDefaultItemRecords;
   g->apply_cps = 0;
   g->apply_threads = (int)(((g->L * g->P) + 31) / 32 * 32);
@@ -489,11 +493,11 @@ cudaError_t setup_update(cupc_graph* g) {
 
 // Shared memory and persistent grid of k_apply for the given tunables.
 cudaError_t apply_config(const cupc_graph* g, uint32_t item_records, uint32_t R, uint32_t cps, int* smem, int* grid) {
-  *smem = (int)apply_smem_bytes(item_records, R, (uint32_t)g->apply_threads);
+  *smem = (int)apply_smem_bytes(R, (uint32_t)g->apply_threads, g->L);
   cudaError_t e = raise_apply_smem_limit(*smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, g->D > 32 ? k_apply<true> : k_apply<false>,
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, g->long_depth ? k_apply<true> : k_apply<false>,
                                                     g->apply_threads, *smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
@@ -545,10 +549,22 @@ cudaError_t launch_update_chunk(cupc_graph* g, const uint32_t* edges, size_t n, 
       k_scatter<<<grid, 256, 0, s>>>(edges, n, g->V, g->cursor, g->rec, g->recw, g->gc);
   }
   ProfScope ps(g, s, PC_APPLY, 1);
-  auto kern = g->D > 32 ? k_apply<true> : k_apply<false>;
+  auto kern = g->long_depth ? k_apply<true> : k_apply<false>;
   kern<<<agrid, g->apply_threads, smem, s>>>(g->sketch, g->keys, g->rec, g->recw, g->items, g->gc, g->V, g->L, g->C,
-                                              g->D, g->W, g->P, R, ir);
+                                              g->D, g->W, g->P, R, g->ell);
   return cudaGetLastError();
 }
 
 }  // namespace cupc
+
+extern "C" cupc_status cupc_build_info(int* binary_version, int* ptx_version) {
+  if (!binary_version || !ptx_version) return CUPC_EINVAL;
+  cudaFuncAttributes fa;
+  if (cudaFuncGetAttributes(&fa, (const void*)cupc::k_apply<false>) != cudaSuccess) {
+    cudaGetLastError();
+    return CUPC_ECUDA;
+  }
+  *binary_version = fa.binaryVersion;
+  *ptx_version = fa.ptxVersion;
+  return CUPC_OK;
+}

@@ -132,78 +132,156 @@ __device__ __forceinline__ void xor_bucket_atomic(ulonglong2* p, ulonglong2 v) {
   atomicXor(&p->y, v.y);
 }
 
-// The SplitMix64 finalizer of idx ^ key, split so that its first step is
-// shared by every lane: with z = idx ^ key, z ^ (z >> 30) equals
-// pre(idx) ^ pre(key), pre(x) = x ^ (x >> 30), because XOR commutes with a
-// logical shift. pre(idx) is computed once per record when the record is
-// staged in shared memory; pre(key) is a per-lane constant.
-__device__ __forceinline__ uint64_t pre_mix(uint64_t x) { return x ^ (x >> 30); }
-__device__ __forceinline__ uint64_t mix_tail(uint64_t z) {
-  z *= 0xBF58476D1CE4E5B9ull;
-  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-  return z ^ (z >> 31);
-}
-
-// Row of an index from its hash: trailing zeros, capped at D-1. With
-// D <= 32 the low hash word decides (a zero low word means depth >= 32 >=
-// D-1); wider sketches fall back to the 64-bit count in that rare case.
-template <bool kWide>
-__device__ __forceinline__ uint32_t depth_fast(uint64_t h, uint32_t D) {
-  const uint32_t lo = (uint32_t)h;
-  uint32_t d = (uint32_t)__ffs(lo) - 1u;  // lo == 0 gives 0xFFFFFFFF
-  if (kWide && lo == 0) d = depth_of(h, D);
-  return min(d, D - 1);
-}
-
 __device__ __forceinline__ void prefetch_l2(const void* p) {
   asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
 }
 
 // What one thread of the apply kernel does for a graph: tid = r*P + s; r < L
-// is the layer, s < C a column, s == C the checksum lane, which owns the
-// deterministic bucket (its row 0). Lanes past the layout are idle: they fold
-// into their own row 0, which is never written back.
+// is the layer, s < C a column, s == C the deterministic bucket. Lanes past
+// the layout are idle: they fold into their own row 0, which is never
+// written back.
+//
+// Column hash (Theorem A.1: 2-wise independent hash functions suffice):
+// multiply-add-shift, h(x) = ((a*x + b) mod 2^64) div 2^(64-ell) with
+// ell = 65 - 2*ceil(log2 V), strongly universal for indices x < V^2
+// (Dietzfelbinger, STACS 1996); a second stage (a', b') continues the bit
+// string when h(x) is zero. The depth is the number of leading zero bits of
+// that string, capped at D-1. The deterministic and idle lanes use a = 0,
+// b = 2^63, whose depth is always 0.
 struct ApplyLane {
-  uint64_t kpre;       // pre(key) of this lane's column (or checksum) hash
-  uint32_t chk_lane;   // warp lane holding the checksum of this lane's layer
-  uint32_t jbase;      // first bucket of this lane's column in its layer
-  uint32_t nrows;      // rows this lane may have to write back
-  uint32_t layer;      // r (0 for idle lanes)
-  bool active, row0;
+  uint64_t ka, kb;       // first-stage words of this lane's column
+  const uint64_t* kx;    // {b, a', b'} of this lane's column (second stage)
+  uint32_t ell, dmax;    // bits per stage, D-1
+  uint32_t jbase;        // first bucket of this lane's column in its layer
+  uint32_t nrows;        // rows this lane may have to write back
+  uint32_t layer;        // r (0 for idle lanes)
+  uint32_t si0, sr0;     // staging: first (record, layer) of this thread
+  uint32_t sqi, sqr;     // staging: blockDim.x as (records, layers)
+  bool active;
 };
 
+// keys: K(r*(C+1) + c) = a of column c (c < C), K(r*(C+1) + C) = checksum
+// key of layer r, K(L*(C+1) + 3*(r*C + c) + {0,1,2}) = b, a', b'.
 __device__ __forceinline__ ApplyLane apply_lane(const uint64_t* keys, uint32_t L, uint32_t C, uint32_t D, uint32_t P,
-                                                uint32_t R) {
+                                                uint32_t R, uint32_t ell) {
   ApplyLane l;
-  const uint32_t tid = threadIdx.x, lane = tid & 31;
+  const uint32_t tid = threadIdx.x;
   const uint32_t r = tid / P, s = tid % P;
+  const bool col = r < L && s < C;
   l.active = r < L && s <= C;
-  l.row0 = !l.active || s == C;
-  l.kpre = l.active ? pre_mix(keys[r * (C + 1) + s]) : 0;
-  l.chk_lane = (lane & ~(P - 1)) | C;
+  const uint64_t* kx = keys + (size_t)L * (C + 1) + 3 * (size_t)(r * C + s);
+  l.ka = col ? keys[r * (C + 1) + s] : 0ull;
+  l.kb = col ? kx[0] : (1ull << 63);
+  l.kx = col ? kx : nullptr;
+  l.ell = ell;
+  l.dmax = D - 1;
   l.jbase = s == C ? 0u : 1u + s * D;
   l.nrows = s == C ? 1u : R;
   l.layer = r < L ? r : 0;
+  l.si0 = tid / L;
+  l.sr0 = tid % L;
+  l.sqi = blockDim.x / L;
+  l.sqr = blockDim.x % L;
   return l;
 }
 
+// The exact depth when the high word of the first stage does not decide it:
+// leading zeros of the 2*ell-bit string h(x) h'(x) (probability 2^-min(ell,32)).
+static __device__ __noinline__ uint32_t depth_long(const ApplyLane& l, uint64_t x, uint64_t z) {
+  uint32_t d = min((uint32_t)__clzll((long long)z), l.ell);
+  if (d == l.ell) {
+    const uint64_t z2 = l.kx[1] * x + l.kx[2];
+    d += min((uint32_t)__clzll((long long)z2), l.ell);
+  }
+  return d;
+}
+
+// Depth of index x in this lane's column. kLong: ell < D-1 or D-1 > 32, so
+// the high word of a*x + b alone may not decide the depth (V > 2^16 at
+// default parameters); otherwise min(clz(high word), D-1) is exact.
+template <bool kLong>
+__device__ __forceinline__ uint32_t lane_depth(const ApplyLane& l, uint64_t x) {
+  const uint64_t z = l.ka * x + l.kb;
+  uint32_t d = (uint32_t)__clz((int)(uint32_t)(z >> 32));
+  if (kLong && d >= min(l.ell, 32u)) d = depth_long(l, x, z);
+  return min(d, l.dmax);
+}
+
+// Shared memory of an apply CTA: fold rows (rows x threads buckets), then
+// the staged records, their per-layer checksums, the layer checksum keys
+// and the records' vertices (direct path).
+struct ApplySmem {
+  ulonglong2* rows;
+  uint64_t* x;     // kStage
+  uint64_t* g;     // kStage * L, [record][layer]
+  uint64_t* kchk;  // L
+  uint32_t* w;     // kStage
+};
+__device__ __forceinline__ ApplySmem apply_smem(unsigned char* raw, uint32_t rows, uint32_t L) {
+  ApplySmem m;
+  m.rows = reinterpret_cast<ulonglong2*>(raw);
+  m.x = reinterpret_cast<uint64_t*>(m.rows + (size_t)rows * blockDim.x);
+  m.g = m.x + kStage;
+  m.kchk = m.g + (size_t)kStage * L;
+  m.w = reinterpret_cast<uint32_t*>(m.kchk + L);
+  return m;
+}
+
+// Fill the layer checksum keys of a graph (call from every thread; the
+// first staging pass's barrier orders it before any use).
+__device__ __forceinline__ void load_kchk(const ApplySmem& m, const uint64_t* keys, uint32_t L, uint32_t C) {
+  for (uint32_t r = threadIdx.x; r < L; r += blockDim.x) m.kchk[r] = keys[r * (C + 1) + C];
+}
+
+// Stage records rec[0..n), n <= kStage: idx, and G_r(idx) for every layer,
+// computed once per (record, layer) and shared by the layer's lanes.
+__device__ __forceinline__ void stage_records(const ApplyLane& l, const ApplySmem& m,
+                                              const uint64_t* __restrict__ rec, const uint32_t* __restrict__ recw,
+                                              uint32_t n, uint32_t L) {
+  const uint32_t total = n * L;
+  uint32_t i = l.si0, r = l.sr0;
+  for (uint32_t k = threadIdx.x; k < total; k += blockDim.x) {
+    const uint64_t x = __ldg(rec + i);
+    if (r == 0) {
+      m.x[i] = x;
+      if (recw) m.w[i] = __ldg(recw + i);
+    }
+    m.g[k] = mix64(x ^ m.kchk[r]);
+    i += l.sqi;
+    r += l.sqr;
+    if (r >= L) {
+      r -= L;
+      i++;
+    }
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ void fold_record(ulonglong2* gb, ulonglong2* my_rows, uint32_t rs, uint32_t R, uint32_t d,
+                                            uint64_t x, uint64_t gm) {
+  if (d < R) {
+    ulonglong2 v = my_rows[d * rs];
+    v.x ^= x;
+    v.y ^= gm;
+    my_rows[d * rs] = v;
+  } else {
+    xor_bucket_atomic(gb + d, make_ulonglong2(x, gm));
+  }
+}
+
 // Fold the records rec[0..n) of one work item into the sketch of its vertex,
-// whose buckets for this lane start at gb. Rows of a lane live at
-// my_rows[d * rs] (rs = blockDim.x), so the 8 lanes of a shared-memory phase
-// always hit 8 distinct 16-byte bank groups; a lane is the only writer of its
-// rows, so no shared atomics are needed, and every lane runs the same
-// branch-free instruction stream. The next record is hashed while the current
-// one folds. The loop is kept this lean on purpose: at <= 64 registers eight
-// 128-thread CTAs fit an SM, and that occupancy hides the shared-memory
-// latency of the fold better than hashing several records ahead (measured on
-// GB300: 462 us for 2^20 edges at V = 16384 against 514 us with a four-record
-// lookahead at 80 registers). `excl`: no other CTA writes this vertex, so the
+// whose buckets for this lane start at gb. Records pass through shared
+// memory kStage at a time. Rows of a lane live at my_rows[d * rs]
+// (rs = blockDim.x), so the lanes of a shared-memory phase hit distinct
+// 16-byte bank groups; a lane is the only writer of its rows, so no shared
+// atomics are needed. Four records at a time: their loads and depths are
+// independent, only the row read-modify-writes form a chain (two records
+// may share a row). `excl`: no other CTA writes this vertex, so the
 // write-back is a plain read-modify-write. Call from every thread.
-template <bool kWide>
+template <bool kLong>
 __device__ __forceinline__ void apply_item(const ApplyLane& l, ulonglong2* gb, const uint64_t* __restrict__ rec,
-                                           uint32_t n, bool excl, uint32_t D, uint32_t R, ulonglong2* s_xp,
+                                           uint32_t n, bool excl, uint32_t L, uint32_t R, const ApplySmem& m,
                                            ulonglong2* my_rows, uint32_t rs) {
-  const uint32_t tid = threadIdx.x;
   if (l.active) {  // bring this lane's buckets to L2 for the write-back
     prefetch_l2(gb);
     if (l.nrows > 1) {
@@ -211,29 +289,29 @@ __device__ __forceinline__ void apply_item(const ApplyLane& l, ulonglong2* gb, c
       prefetch_l2(gb + l.nrows - 1);
     }
   }
-  for (uint32_t i = tid; i < n; i += blockDim.x) {
-    const uint64_t x = rec[i];
-    s_xp[i] = make_ulonglong2(x, pre_mix(x));
-  }
-  __syncthreads();
-
-  ulonglong2 xc = s_xp[0];
-  uint64_t hc = mix_tail(xc.y ^ l.kpre);
-  for (uint32_t i = 0; i < n; i++) {
-    const uint64_t gm = __shfl_sync(0xffffffffu, hc, l.chk_lane);
-    const ulonglong2 xn = s_xp[min(i + 1, n - 1)];  // the last one is recomputed harmlessly
-    const uint64_t hn = mix_tail(xn.y ^ l.kpre);
-    const uint32_t d = l.row0 ? 0u : depth_fast<kWide>(hc, D);
-    if (d < R) {
-      ulonglong2 v = my_rows[d * rs];
-      v.x ^= xc.x;
-      v.y ^= gm;
-      my_rows[d * rs] = v;
-    } else {
-      xor_bucket_atomic(gb + d, make_ulonglong2(xc.x, gm));
+  const uint64_t* gcol = m.g + l.layer;
+  const ulonglong2* x2 = reinterpret_cast<const ulonglong2*>(m.x);
+  for (uint32_t c0 = 0; c0 < n; c0 += kStage) {
+    const uint32_t nc = min(kStage, n - c0);
+    if (c0) __syncthreads();  // every lane is done with the previous pass
+    stage_records(l, m, rec + c0, nullptr, nc, L);
+    uint32_t i = 0;
+    for (; i + 4 <= nc; i += 4) {
+      const ulonglong2 xa = x2[i >> 1], xb = x2[(i >> 1) + 1];
+      const uint64_t x[4] = {xa.x, xa.y, xb.x, xb.y};
+      uint64_t gm[4];
+      uint32_t d[4];
+#pragma unroll
+      for (int k = 0; k < 4; k++) gm[k] = gcol[(i + k) * L];
+#pragma unroll
+      for (int k = 0; k < 4; k++) d[k] = lane_depth<kLong>(l, x[k]);
+#pragma unroll
+      for (int k = 0; k < 4; k++) fold_record(gb, my_rows, rs, R, d[k], x[k], gm[k]);
     }
-    xc = xn;
-    hc = hn;
+    for (; i < nc; i++) {
+      const uint64_t x = m.x[i];
+      fold_record(gb, my_rows, rs, R, lane_depth<kLong>(l, x), x, gcol[i * L]);
+    }
   }
 
   // write back only the touched (non-zero) rows of this vertex
@@ -274,36 +352,33 @@ __device__ __forceinline__ void apply_item(const ApplyLane& l, ulonglong2* gb, c
   __syncthreads();
 }
 
-
 // Direct-path item: records of several vertices, each record's buckets XORed
 // straight into HBM (atomics, no write-back). recw[i] is record i's vertex.
-template <bool kWide>
+template <bool kLong>
 __device__ __forceinline__ void apply_direct(const ApplyLane& l, ulonglong2* sketch, uint32_t V, uint32_t W,
                                              const uint64_t* __restrict__ rec, const uint32_t* __restrict__ recw,
-                                             uint32_t n, uint32_t D, ulonglong2* s_xp, uint32_t* s_w) {
-  const uint32_t tid = threadIdx.x;
-  for (uint32_t i = tid; i < n; i += blockDim.x) {
-    const uint64_t x = rec[i];
-    s_xp[i] = make_ulonglong2(x, pre_mix(x));
-    s_w[i] = recw[i];
-  }
-  __syncthreads();
+                                             uint32_t n, uint32_t L, const ApplySmem& m) {
   ulonglong2* lbase = sketch + (size_t)l.layer * V * W + l.jbase;
-  for (uint32_t i0 = 0; i0 < n; i0 += 4) {
-    ulonglong2 x[4];
-    uint64_t h[4], g[4];
+  const uint64_t* gcol = m.g + l.layer;
+  for (uint32_t c0 = 0; c0 < n; c0 += kStage) {
+    const uint32_t nc = min(kStage, n - c0);
+    if (c0) __syncthreads();
+    stage_records(l, m, rec + c0, recw + c0, nc, L);
+    for (uint32_t i0 = 0; i0 < nc; i0 += 4) {
+      uint64_t x[4], gm[4];
+      uint32_t d[4], w[4];
 #pragma unroll
-    for (uint32_t k = 0; k < 4; k++) {
-      x[k] = s_xp[min(i0 + k, n - 1)];
-      h[k] = mix_tail(x[k].y ^ l.kpre);
-    }
+      for (uint32_t k = 0; k < 4; k++) {
+        const uint32_t i = min(i0 + k, nc - 1);
+        x[k] = m.x[i];
+        gm[k] = gcol[i * L];
+        w[k] = m.w[i];
+      }
 #pragma unroll
-    for (uint32_t k = 0; k < 4; k++) g[k] = __shfl_sync(0xffffffffu, h[k], l.chk_lane);
+      for (uint32_t k = 0; k < 4; k++) d[k] = lane_depth<kLong>(l, x[k]);
 #pragma unroll
-    for (uint32_t k = 0; k < 4; k++) {
-      uint32_t d = depth_fast<kWide>(h[k], D);
-      if (l.row0) d = 0;
-      if (l.active && i0 + k < n) xor_bucket_atomic(lbase + (size_t)s_w[i0 + k] * W + d, make_ulonglong2(x[k].x, g[k]));
+      for (uint32_t k = 0; k < 4; k++)
+        if (l.active && i0 + k < nc) xor_bucket_atomic(lbase + (size_t)w[k] * W + d[k], make_ulonglong2(x[k], gm[k]));
     }
   }
   __syncthreads();

@@ -66,6 +66,7 @@ _SIGS = {
     "cupc_destroy": (None, [_P]),
     "cupc_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "cupc_selftest_wait_timeout": (ctypes.c_int, [_u32, _u32, ctypes.c_int, _P]),
+    "cupc_build_info": (ctypes.c_int, [_P, _P]),
     "cupc_update_sketch_static": (ctypes.c_int, [_P, _u32, _u64, _P, _P, _sz, _P, _P]),
 }
 for _name, (_res, _args) in _SIGS.items():
@@ -278,6 +279,13 @@ def cupc_destroy(g) -> None:
 
 def cupc_selftest_wait_timeout(ctas: int, limit_us: int, absent_cta: int, stream=None) -> int:
     return _lib.cupc_selftest_wait_timeout(ctas, limit_us, absent_cta, stream_handle(stream))
+
+
+def cupc_build_info():
+    """Returns (status, binary_version, ptx_version) of the update kernel."""
+    b, p = ctypes.c_int(0), ctypes.c_int(0)
+    st = _lib.cupc_build_info(ctypes.byref(b), ctypes.byref(p))
+    return st, b.value, p.value
 
 
 def cupc_status_string(st: int) -> str:

@@ -383,3 +383,13 @@ def test_bounded_device_wait_reports_timeout_and_context_survives():
     ref.update(E)
     assert np.array_equal(dev.export(), ref.export())
     assert C.cupc_selftest_wait_timeout(1, 100, -1) == C.CUPC_EINVAL
+
+
+def test_kernels_are_built_for_sm_103a():
+    # what the CUDA runtime loaded for this device: SASS for compute 10.3
+    from paper_2509_14433_gb300 import cupc as C
+    st, binary, ptx = C.cupc_build_info()
+    assert st == C.CUPC_OK
+    assert binary == 103, binary
+    major, minor = torch.cuda.get_device_capability(0)
+    assert (major, minor) == (10, 3)
