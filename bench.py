@@ -753,12 +753,27 @@ def batch_latency_sweep(torch, C, g, D_d, ins_d, del_d, p_d, q_out, stream):
 
 
 def run_apply_profile(args):
-    """Small case for ncu: a V=16384 graph (826 MB of sketches, larger than
-    L2) receives the first 8 insert batches of the dense stream."""
+    """Small cases for ncu. dense: a V=16384 graph (826 MB of sketches,
+    larger than L2) receives the first 8 insert batches of the dense stream.
+    rmat: a V=2^15 graph (1.9 GB of sketches) receives 6 R-MAT batches of
+    2^20..2^22 edges (the batched workload's generator at 15 levels)."""
     import torch
 
     from paper_2509_14433_gb300 import cupc as C
     torch.cuda.set_device(0)
+    if args.profile_case == "rmat":
+        V = 1 << 15
+        s = WL.RmatStream(levels=15, seed=3, batch_lo=1 << 20, batch_hi=4 << 20, device="cuda")
+        bl = [s.next_batch() for _ in range(6)]
+        stream = torch.cuda.current_stream()
+        st, g = C.cupc_init(V, SEED, (0, 0, 0, 4 << 20), None, stream)
+        C.check(st)
+        for e, o in bl:
+            C.check(C.cupc_update_batch(g, e.reshape(-1).contiguous(), o.contiguous(), len(o), stream))
+        C.check(C.cupc_sync(g, stream))
+        C.cupc_destroy(g)
+        print("apply-profile rmat done", [len(o) for _, o in bl])
+        return
     E, _ = make_dense_stream()
     n = 8 * BATCH
     E_d = torch.from_numpy(E[:n].reshape(-1)).cuda()
@@ -788,6 +803,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batching", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--profile-case", default="dense", choices=["dense", "rmat"])
     args = ap.parse_args()
     if args.mode == "apply-profile":
         run_apply_profile(args)
