@@ -1,19 +1,25 @@
 """Throughput benchmark of the sketch-connectivity hot path on GB300.
 
-Workload (one step = one whole job, inputs resident in HBM before timing):
-  dense V=16384: all edges of an Erdos-Renyi G(V, 0.5) graph (~67.1M) inserted
-  in a seeded random order in batches of 2^20, then a uniform random 10% of
-  them deleted in batches of 2^20, then the spanning forest. Sketches (826 MB)
-  and the edge stream (~600 MB) are larger than L2, so no flush is needed.
+Headline workload (one step = one whole job, inputs resident in HBM before
+timing): the batched R-MAT stream on V = 2^17 vertices, (a, b, c, d) =
+(.57, .19, .19, .05), 1e9 updates of which 20% delete previously inserted
+edges, in batches of log-uniform size in [1k, 4M], applied as back-to-back
+batches (cupc_update_batches: coalesced into 4M-edge launches of the
+persistent apply kernel with autotuned per-size settings), then one 1k-pair
+Connected batch (the Boruvka recovery) and the spanning forest. The stream
+(9 GB) and the sketches (9.5 GB) are larger than L2, so no flush is needed.
 value = edge updates per second over the whole job (all ranks).
 
-Also reported: the same job end to end through the C-ABI with pinned host
-buffers (e2e), Connected-query latency p50/p99 on the plain V=1024 toggle
-stream and right after a dense batch, the live roofline of the dominant
-kernel (the sketch apply kernel) and the CPU oracle timed on a bounded sample.
+Also reported: the same job end to end through the C-ABI from pinned host
+buffers (e2e), the one-batch-per-launch arm, the live roofline of the
+dominant kernel (the sketch apply kernel), the other workloads (plain
+V=1024 toggle stream, dense V=16384, 64-graph serving closed and open loop,
+256 cliques on V=2^17, the paper's stream shapes) with query p50/p99 over
+at least 1000 query batches each, and the CPU oracle timed on a stated
+bounded sample of each.
 
---impl reference times the CPU oracle on the same workload (bounded sample
-per step) and prints the same JSON line with "impl": "reference".
+--impl reference times the CPU oracle on the headline workload (a bounded
+sample per step) and prints the same JSON line with "impl": "reference".
 """
 from __future__ import annotations
 
@@ -34,9 +40,14 @@ from paper_2509_14433_gb300 import workloads as WL  # noqa: E402
 
 METRIC = "edge updates/s and p99 Connected-query latency on 1 GB300, bit-exact; HBM GB/s"
 UNIT = "edge updates/s"
-V_DENSE, P_DENSE, BATCH, SEED = 16384, 0.5, 1 << 20, 1
-CPU_SAMPLE_BATCHES = 2
-REF_SAMPLE_BATCHES = 1
+SEED = 1  # hash seed of every graph
+# headline: the batched R-MAT workload
+V_RMAT, RMAT_LEVELS, RMAT_UPDATES, RMAT_SEED, MAXB = 1 << 17, 17, 1_000_000_000, 3, 4 << 20
+# dense ER(0.5) workload
+V_DENSE, P_DENSE, BATCH = 16384, 0.5, 1 << 20
+QUERY_SAMPLES = 1000  # query batches behind every p50/p99
+CPU_RMAT_SAMPLE = 1 << 19  # headline oracle sample (updates)
+REF_RMAT_SAMPLE = 1 << 18  # reference arm sample per step (updates)
 
 
 def dist_env():
@@ -61,25 +72,29 @@ def whole_job_rate(units_per_step: int, steps: int, world: int, max_ms: float) -
     return units_per_step * steps * world / (max_ms / 1e3)
 
 
-def make_dense_stream():
-    E, n_del, order = WL.dense_stream(V=V_DENSE, p=P_DENSE, batch=BATCH, delete_frac=0.1, seed=SEED)
-    return E, E[order[:n_del]]
+def pcts(lat_us):
+    a = np.asarray(lat_us, np.float64)
+    return {"p50_us": float(np.percentile(a, 50)), "p99_us": float(np.percentile(a, 99)), "samples": int(a.size)}
 
 
-def workload_config(nE, nD):
-    return {"workload": f"dense ER(V={V_DENSE}, p={P_DENSE}): {nE} inserts + {nD} deletes (10%) in batches of "
-                        f"{BATCH}, then spanning forest",
-            "V": V_DENSE, "batch": BATCH, "updates_per_step": nE + nD, "seed": SEED,
-            "apply_tuning": "autotuned table (paper_2509_14433_gb300/tuning_gb300.json) when present",
-            "l2": "inputs larger than L2 (sketches 826 MB, edge stream ~600 MB): no flush"}
+def headline_config(n, nb, sizes):
+    return {"workload": f"batched R-MAT(V={V_RMAT}, a=.57 b=.19 c=.19 d=.05): {n} updates (20% deletes of present "
+                        f"edges) in {nb} batches of log-uniform size in [1000, {MAXB}] (min {min(sizes)}, max "
+                        f"{max(sizes)}), applied back to back in {MAXB}-edge launches, then a 1k-pair Connected "
+                        "batch and the spanning forest",
+            "V": V_RMAT, "updates_per_step": int(n), "batches": int(nb), "max_launch_edges": MAXB,
+            "stream_seed": RMAT_SEED, "hash_seed": SEED,
+            "apply_tuning": "autotuned per batch-size bucket (paper_2509_14433_gb300/tuning_gb300.json)",
+            "l2": "inputs larger than L2 (sketches 9.5 GB, edge stream 9 GB): no flush"}
 
 
 def expected_touched_buckets(counts, L, C, D):
     """Expected distinct buckets an update batch touches, given the number of
     batch records n_w of each vertex: per vertex and layer, the deterministic
     bucket plus, per column, sum_d 1 - (1 - p_d)^n_w with p_d = 2^-(d+1)
-    (the last row takes the tail 2^-(D-1)). Hash values are uniform, so the
-    sum over ~10^6 independent columns is tight around this expectation."""
+    (the last row takes the tail 2^-(D-1)). Depths are uniform over the hash
+    keys, so the sum over ~10^6 independent columns is tight around this
+    expectation."""
     vals, mult = np.unique(counts[counts > 0], return_counts=True)
     p = 2.0 ** -(np.arange(D) + 1.0)
     p[-1] = 2.0 ** -(D - 1)
@@ -97,8 +112,7 @@ def dense_sweep_bytes(counts, L, W):
 def apply_source_digest():
     """md5 over the source k_apply compiles from: the shared device header
     (update_dev.cuh), the kernel's own text in update.cu, and the device
-    functions and error/counter constants of common.cuh (its other
-    declarations serve other kernels and the host)."""
+    functions and constants of common.cuh it uses."""
     import hashlib
     import re
     csrc = os.path.join(ROOT, "paper_2509_14433_gb300", "csrc")
@@ -110,22 +124,22 @@ def apply_source_digest():
     com = open(os.path.join(csrc, "common.cuh")).read()
     for m in re.finditer(r"^__(?:host__ __)?device__ .*?\n}\n|^__device__ [^\n]*}\n", com, re.S | re.M):
         h.update(m.group(0).encode())
-    for m in re.finditer(r"^constexpr uint32_t k(?:ErrInval|DirectItem\w*|SmemRows\w*|\w*ItemRecords) = [^;]*;|^  GC_(?:ERR|NITEMS|NEXT_ITEM) = \d+",
-                         com, re.M):
+    for m in re.finditer(r"^constexpr uint32_t k(?:ErrInval|DirectItem\w*|SmemRows\w*|\w*ItemRecords|Stage) = [^;]*;"
+                         r"|^  GC_(?:ERR|NITEMS|NEXT_ITEM) = \d+", com, re.M):
         h.update(m.group(0).encode())
     return h.hexdigest()
 
 
-def apply_traffic(setting):
-    """DRAM bytes per k_apply launch from the committed ncu summary; None
-    when the kernel's source or its launch setting changed since the
-    counters were taken."""
+def apply_traffic(workload):
+    """DRAM bytes per k_apply launch on this workload from the committed ncu
+    summary; None when the kernel's source changed since the counters were
+    taken or the summary covers another workload."""
     tp = os.path.join(ROOT, "profiles", "k_apply_traffic.json")
     try:
         rec = json.load(open(tp))
     except (OSError, ValueError):
         return None
-    if rec.get("source_md5") != apply_source_digest() or list(rec.get("setting", [])) != list(setting):
+    if rec.get("source_md5") != apply_source_digest() or rec.get("workload") != workload:
         return None
     return rec.get("bytes_per_launch")
 
@@ -167,57 +181,160 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def oracle_sample(E, batches=CPU_SAMPLE_BATCHES, seed=SEED):
-    """CPU oracle on a bounded sample: the first `batches` insert batches of
-    the dense stream, one 1k-pair Connected batch (which runs the recovery),
-    then the spanning forest (one thread). Returns the updates, the time of
-    the whole sample and the time of the query batch."""
+# ---- inputs -----------------------------------------------------------------
+
+def gen_rmat_stream(torch, dev, n_updates=RMAT_UPDATES, seed=RMAT_SEED):
+    """The batched workload's stream, generated on `dev` and stored back to
+    back: edges int32 [n, 2], ops int8 [n], batch offsets (k+1, host)."""
+    s = WL.RmatStream(levels=RMAT_LEVELS, seed=seed, device=dev)
+    cap = n_updates + MAXB
+    E = torch.empty((cap, 2), dtype=torch.int32, device=dev)
+    O = torch.empty(cap, dtype=torch.int8, device=dev)
+    offs = [0]
+    while offs[-1] < n_updates:
+        e, o = s.next_batch()
+        a, n = offs[-1], len(o)
+        E[a:a + n] = e
+        O[a:a + n] = o
+        offs.append(a + n)
+    fallbacks = s.fallbacks
+    del s
+    torch.cuda.empty_cache()
+    n = offs[-1]
+    return E[:n], O[:n], np.array(offs, np.uint64), fallbacks
+
+
+def make_dense_stream():
+    E, n_del, order = WL.dense_stream(V=V_DENSE, p=P_DENSE, batch=BATCH, delete_frac=0.1, seed=SEED)
+    return E, E[order[:n_del]]
+
+
+# ---- CPU oracle samples (bounded; one thread) --------------------------------
+
+def oracle_rmat_sample(E_h, n):
+    """The oracle on the first n updates of the headline stream (one batch),
+    one 1k-pair Connected batch (the recovery) and the spanning forest."""
     import oracle as O
-    n = batches * BATCH
-    pairs = WL.uniform_pairs(V_DENSE, 1000, WL.rng(seed + 7), distinct=False)
-    g = O.Graph(V_DENSE, seed)
+    pairs = WL.uniform_pairs(V_RMAT, 1000, WL.rng(SEED + 7), distinct=False)
+    g = O.Graph(V_RMAT, SEED)
     t = time.perf_counter()
-    for i in range(0, n, BATCH):
-        assert g.update(E[i:i + BATCH]) == O.OK
+    assert g.update(E_h[:n]) == O.OK
     tq = time.perf_counter()
-    s, a = g.query(pairs)
+    s, _ = g.query(pairs)
     tq = time.perf_counter() - tq
     assert s in (O.OK, O.EINCOMPLETE)
-    s, f = g.spanning_forest()
+    g.spanning_forest()
     dt = time.perf_counter() - t
     g.close()
-    return n, dt, tq
+    return dt, tq
 
+
+def cpu_samples(E_rmat_h, dense_E, plain_steps, cl, bridge_batch, serving_one):
+    """The oracle timed on a stated sample of every workload."""
+    import oracle as O
+    out = {}
+    dt, tq = oracle_rmat_sample(E_rmat_h, CPU_RMAT_SAMPLE)
+    out["rmat_v131072"] = {"updates_per_s": CPU_RMAT_SAMPLE / dt, "query_batch_ms": 1e3 * tq,
+                           "sample": f"first {CPU_RMAT_SAMPLE} updates + 1k-pair Connected batch + forest"}
+    n = 2 * BATCH
+    g = O.Graph(V_DENSE, SEED)
+    t = time.perf_counter()
+    g.update(dense_E[:n])
+    tq = time.perf_counter()
+    g.query(WL.uniform_pairs(V_DENSE, 1000, WL.rng(8), distinct=False))
+    tq = time.perf_counter() - tq
+    dt = time.perf_counter() - t
+    g.close()
+    out["dense_v16384"] = {"updates_per_s": n / dt, "query_batch_ms": 1e3 * tq,
+                           "sample": f"first {n} inserts + 1k-pair Connected batch"}
+    g = O.Graph(1024, SEED)
+    nu, lat = 0, []
+    t = time.perf_counter()
+    for st in plain_steps:
+        if st[0] == "update":
+            g.update(st[1], st[2])
+            nu += len(st[2])
+        else:
+            t1 = time.perf_counter()
+            g.query(st[1])
+            lat.append(time.perf_counter() - t1)
+    dt = time.perf_counter() - t
+    g.close()
+    out["plain_v1024"] = {"updates_per_s": nu / (dt - sum(lat)), "query_batch_ms_p50": 1e3 * float(np.median(lat)),
+                          "sample": "the whole stream (start graph, 200k toggles, 20 query batches)"}
+    n = 1 << 20
+    g = O.Graph(131072, SEED)
+    t = time.perf_counter()
+    g.update(cl[:n])
+    g.update(bridge_batch)
+    tq = time.perf_counter()
+    g.query(WL.uniform_pairs(131072, 1000, WL.rng(9), distinct=False))
+    tq = time.perf_counter() - tq
+    dt = time.perf_counter() - t
+    g.close()
+    out["cliques_v131072"] = {"updates_per_s": (n + 65536) / dt, "query_batch_ms": 1e3 * tq,
+                              "sample": f"first {n} clique edges + one 64k bridge batch + 1k-pair Connected batch"}
+    V, seed_i, steps, nupd = serving_one
+    g = O.Graph(V, seed_i)
+    t = time.perf_counter()
+    for st in steps:
+        if st[0] == "update":
+            g.update(st[1], st[2])
+        else:
+            g.query(st[1])
+    dt = time.perf_counter() - t
+    g.close()
+    out["serving_64_graphs"] = {"updates_per_s": nupd / dt,
+                                "sample": f"one graph's whole stream (V={V}, {nupd} updates with its query batches)"}
+    return out
+
+
+# ---- reference arm ------------------------------------------------------------
 
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    E, D = make_dense_stream()
+    import torch
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    # the headline stream's first batches (same generator and seed)
+    s = WL.RmatStream(levels=RMAT_LEVELS, seed=RMAT_SEED, device=dev)
+    parts, n, sizes = [], 0, []
+    while n < REF_RMAT_SAMPLE:
+        e, _ = s.next_batch()
+        parts.append(e.cpu().numpy().astype(np.uint32))
+        n += len(e)
+        sizes.append(len(e))
+    E_h = np.concatenate(parts)
+    del s
+    cfg = headline_config(RMAT_UPDATES, 0, [1000, MAXB])
+    cfg["sample"] = (f"per step: the oracle on the first {REF_RMAT_SAMPLE} updates of this stream, one 1k-pair "
+                     "Connected batch and the spanning forest (single thread)")
     for _ in range(args.warmup):
-        oracle_sample(E, REF_SAMPLE_BATCHES)
-    times, qtimes, n = [], [], 0
+        oracle_rmat_sample(E_h, REF_RMAT_SAMPLE)
+    times, qtimes = [], []
     for _ in range(args.steps):
-        n, dt, tq = oracle_sample(E, REF_SAMPLE_BATCHES)
+        dt, tq = oracle_rmat_sample(E_h, REF_RMAT_SAMPLE)
         times.append(dt)
         qtimes.append(tq)
     tot = sum(times)
-    val = n * args.steps / tot
+    val = REF_RMAT_SAMPLE * args.steps / tot
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
-            "data": "synthetic", "config": workload_config(len(E), len(D)),
-            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"first {n} inserts of the dense stream + one 1k-pair Connected "
-                                       "batch + spanning forest per step",
+            "data": "synthetic", "config": cfg, "units_per_step": REF_RMAT_SAMPLE,
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": cfg["sample"],
                              "query_batch_ms_p50": 1e3 * float(np.median(qtimes))},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
+# ---- GPU arm ------------------------------------------------------------------
+
 def run_gpu(args):
     import torch
 
+    from paper_2509_14433_gb300 import autotune as AT
     from paper_2509_14433_gb300 import cupc as C
 
     rank, world, local = dist_env()
@@ -233,32 +350,30 @@ def run_gpu(args):
         if pg is not None:
             pg.barrier()
 
-    E, D = make_dense_stream()
-    nE, nD = len(E), len(D)
     stream = torch.cuda.current_stream()
-    E_d = torch.from_numpy(E.reshape(-1)).to(dev)
-    D_d = torch.from_numpy(D.reshape(-1)).to(dev)
-    ins_d = torch.ones(nE, dtype=torch.int8, device=dev)
-    del_d = torch.full((nD,), -1, dtype=torch.int8, device=dev)
-    forest_d = torch.empty(V_DENSE, dtype=torch.int64, device=dev)
-    st, g = C.cupc_init(V_DENSE, SEED, None, None, stream)
+    t_gen = time.perf_counter()
+    E, O, offs, fallbacks = gen_rmat_stream(torch, dev)
+    t_gen = time.perf_counter() - t_gen
+    n, nb = int(offs[-1]), len(offs) - 1
+    sizes = np.diff(offs).astype(np.int64)
+    V = V_RMAT
+    st, g = C.cupc_init(V, SEED, (0, 0, 0, MAXB), None, stream)
     C.check(st, "cupc_init")
-    from paper_2509_14433_gb300 import autotune as AT
-    tuned = AT.apply(g, V_DENSE, BATCH)  # tuned apply setting for 2^20-edge batches, if the table has one
-    tun = np.zeros(4, np.uint32)
-    C.cupc_get_tuning(g, tun)
-    apply_setting = [int(x) for x in tun[:3]]
+    n_buckets = AT.apply_buckets(g, V)
     prm = np.zeros(4, np.uint32)
     C.cupc_get_params(g, prm)
     L, Cc, Dd, W = (int(x) for x in prm)
+    pairs = WL.uniform_pairs(V, 1000, WL.rng(77), distinct=False)
+    P_d = torch.from_numpy(pairs.reshape(-1)).to(dev)
+    q_out = torch.empty(1000, dtype=torch.uint8, device=dev)
+    forest_d = torch.empty(V, dtype=torch.int64, device=dev)
+    Eflat = E.reshape(-1)
 
     def step_device():
         C.check(C.cupc_reset(g, stream))
-        for i in range(0, nE, BATCH):
-            C.check(C.cupc_update_batch(g, E_d[2 * i:], ins_d[i:], min(BATCH, nE - i), stream))
-        for i in range(0, nD, BATCH):
-            C.check(C.cupc_update_batch(g, D_d[2 * i:], del_d[i:], min(BATCH, nD - i), stream))
-        st, nf = C.cupc_spanning_forest(g, forest_d, V_DENSE, stream)
+        C.check(C.cupc_update_batches(g, Eflat, O, offs, nb, stream))
+        C.check(C.cupc_query(g, P_d, 1000, q_out, stream), "query", ok=(C.CUPC_OK, C.CUPC_EINCOMPLETE))
+        st, nf = C.cupc_spanning_forest(g, forest_d, V, stream)
         C.check(st, "spanning_forest", ok=(C.CUPC_OK, C.CUPC_EINCOMPLETE))
         return nf
 
@@ -283,24 +398,27 @@ def run_gpu(args):
     ms = ev0.elapsed_time(ev1)
     barrier()
     ms = max_over_ranks(ms, dev)
-    upd_per_step = nE + nD
-    value = whole_job_rate(upd_per_step, args.steps, world, ms)
+    value = whole_job_rate(n, args.steps, world, ms)
     assert C.cupc_sync(g, stream) == C.CUPC_OK
 
-    # ---- e2e: the same job through the C-ABI with pinned host buffers
-    E_h = torch.from_numpy(E.reshape(-1)).pin_memory()
-    D_h = torch.from_numpy(D.reshape(-1)).pin_memory()
-    ins_h = torch.ones(nE, dtype=torch.int8).pin_memory()
-    del_h = torch.full((nD,), -1, dtype=torch.int8).pin_memory()
-    forest_h = torch.empty(V_DENSE, dtype=torch.int64).pin_memory()
+    # ---- e2e: the same job through the C-ABI from pinned host buffers, in
+    # calls of at most MAXB edges (each copy overlaps the previous launch)
+    E_h = torch.empty(E.shape, dtype=torch.int32, pin_memory=True)
+    E_h.copy_(E)
+    O_h = torch.empty(O.shape, dtype=torch.int8, pin_memory=True)
+    O_h.copy_(O)
+    P_h = torch.from_numpy(pairs.reshape(-1).copy()).pin_memory()
+    q_h = torch.empty(1000, dtype=torch.uint8).pin_memory()
+    forest_h = torch.empty(V, dtype=torch.int64).pin_memory()
+    e_ptr, o_ptr = E_h.data_ptr(), O_h.data_ptr()
 
     def step_host():
         C.check(C.cupc_reset(g, stream))
-        for i in range(0, nE, BATCH):
-            C.check(C.cupc_update_batch(g, E_h.data_ptr() + 8 * i, ins_h.data_ptr() + i, min(BATCH, nE - i), stream))
-        for i in range(0, nD, BATCH):
-            C.check(C.cupc_update_batch(g, D_h.data_ptr() + 8 * i, del_h.data_ptr() + i, min(BATCH, nD - i), stream))
-        st, nf = C.cupc_spanning_forest(g, forest_h, V_DENSE, stream)
+        for i in range(0, n, MAXB):
+            k = min(MAXB, n - i)
+            C.check(C.cupc_update_batch(g, e_ptr + 8 * i, o_ptr + i, k, stream))
+        C.check(C.cupc_query(g, P_h, 1000, q_h, stream), "query", ok=(C.CUPC_OK, C.CUPC_EINCOMPLETE))
+        st, nf = C.cupc_spanning_forest(g, forest_h, V, stream)
         C.check(st, "spanning_forest", ok=(C.CUPC_OK, C.CUPC_EINCOMPLETE))
         return nf
 
@@ -308,50 +426,71 @@ def run_gpu(args):
     torch.cuda.synchronize()
     barrier()
     t0 = time.perf_counter()
-    e2e_steps = max(3, min(args.steps, 5))  # at least 3: one slow step must not set the number
+    e2e_steps = 3
     for _ in range(e2e_steps):
         nf_h = step_host()
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     barrier()
     e2e_s = max_over_ranks(e2e_s, dev)
-    e2e_val = whole_job_rate(upd_per_step, e2e_steps, world, e2e_s * 1e3)
+    e2e_val = whole_job_rate(n, e2e_steps, world, e2e_s * 1e3)
     assert nf_h == nf and torch.equal(forest_h[:nf], forest_d[:nf].cpu())
+    assert torch.equal(q_h, q_out.cpu())
+    E_cpu_sample = E_h[:max(CPU_RMAT_SAMPLE, REF_RMAT_SAMPLE)].numpy().astype(np.uint32).copy()
+    del E_h, O_h
 
-    # ---- Connected-query latency right after a dense update batch
-    lat_dense = []
-    pairs = WL.uniform_pairs(V_DENSE, 1000, WL.rng(77), distinct=False)
-    p_d = torch.from_numpy(pairs.reshape(-1)).to(dev)
-    q_out = torch.empty(1000, dtype=torch.uint8, device=dev)
-    for k in range(12):
-        i = (k % 6) * BATCH  # toggle one 2^20-edge batch, then ask
-        C.check(C.cupc_update_batch(g, E_d[2 * i:], ins_d[i:], BATCH, stream))
-        torch.cuda.synchronize()
-        t = time.perf_counter()
-        C.check(C.cupc_query(g, p_d, 1000, q_out, stream))
-        torch.cuda.synchronize()
-        lat_dense.append((time.perf_counter() - t) * 1e6)
-    sweep = batch_latency_sweep(torch, C, g, D_d, ins_d, del_d, p_d, q_out, stream)
-    C.cupc_destroy(g)
-    del E_d, D_d, ins_d, del_d
+    rows, extra = {}, {}
+    if rank == 0 and world == 1:
+        # ---- the same stream one batch per launch (updates only, both arms)
+        def upd_coalesced():
+            C.check(C.cupc_update_batches(g, Eflat, O, offs, nb, stream))
 
-    # ---- plain V=1024 toggle stream: updates/s and query latency
-    plain = plain_stream_latency(torch, C, dev, stream)
-    plain.update(plain_stream_latency(torch, C, dev, stream, inc=1))
-    pstream = None if args.no_batching else paper_stream(torch, C, dev, stream)
-    batching = None if args.no_batching else batching_compare(torch, C, dev, stream)
-    serving = None if args.no_serving else serving_compare(torch, C, dev)
+        def upd_plain():
+            for i in range(nb):
+                a = int(offs[i])
+                C.check(C.cupc_update_batch(g, E[a:].reshape(-1), O[a:], int(sizes[i]), stream))
 
-    # ---- roofline of the dominant kernel (sketch apply), measured live above
-    counts_per_batch = []
-    for i in range(0, nE, BATCH):
-        counts_per_batch.append(np.bincount(E[i:i + BATCH].reshape(-1), minlength=V_DENSE))
-    for i in range(0, nD, BATCH):
-        counts_per_batch.append(np.bincount(D[i:i + BATCH].reshape(-1), minlength=V_DENSE))
-    touched = [expected_touched_buckets(c, L, Cc, Dd) for c in counts_per_batch]
+        arms = {}
+        for name, fn in (("coalesced_4M_launches", upd_coalesced), ("one_batch_per_launch", upd_plain)):
+            C.check(C.cupc_reset(g, stream))
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            arms[name] = n / (e0.elapsed_time(e1) / 1e3)
+        extra["batched_vs_one_batch_per_launch"] = {"updates": n, "batches": nb, "updates_per_s": arms,
+                                                    "fallback_uniform_inserts": int(fallbacks),
+                                                    "stream_generation_s": t_gen}
+        # ---- query latency on the final graph: a 1k-pair Connected batch
+        # right after an update batch (a toggle of the stream's last 64k
+        # updates, so the recovery runs); host submit -> answers ready
+        lat = []
+        tail = max(0, n - 65536)
+        for k in range(QUERY_SAMPLES + 5):
+            C.check(C.cupc_update_batch(g, E[tail:].reshape(-1), O[tail:], n - tail, stream))
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            C.check(C.cupc_query(g, P_d, 1000, q_out, stream), "query", ok=(C.CUPC_OK, C.CUPC_EINCOMPLETE))
+            torch.cuda.synchronize()
+            if k >= 5:
+                lat.append((time.perf_counter() - t) * 1e6)
+        rows["rmat_v131072"] = {"updates_per_s": value, "e2e_updates_per_s": e2e_val,
+                                "queries_per_s_in_query_batches": 1000 / (np.mean(lat) * 1e-6),
+                                "query_after_64k_batch": pcts(lat), "forest_edges": int(nf)}
+
+    # ---- roofline of the dominant kernel (sketch apply), measured live in
+    # the timed steps: algorithmic bytes of every launch (from its chunk's
+    # vertex counts) over the launches' CUDA-event time
+    touched, sweep = [], []
+    for i in range(0, n, MAXB):
+        cnt = torch.bincount(Eflat[2 * i:2 * min(n, i + MAXB)].long(), minlength=V).cpu().numpy()
+        touched.append(expected_touched_buckets(cnt, L, Cc, Dd))
+        sweep.append(dense_sweep_bytes(cnt, L, W))
     apply_bytes_per_launch = 32.0 * float(np.mean(touched))
-    sweep_bytes_per_launch = float(np.mean([dense_sweep_bytes(c, L, W) for c in counts_per_batch]))
     apply_launches = int(nl_prof[2])
+    assert apply_launches == args.steps * len(touched), (apply_launches, len(touched))
     apply_ms = ms_prof[2] / max(1, apply_launches)
     peaks = {}
     try:
@@ -360,102 +499,262 @@ def run_gpu(args):
         pass
     peak = float(peaks.get("hbm_gbs", 6800.0))
     achieved = apply_bytes_per_launch / (apply_ms * 1e-3) / 1e9
-    traffic = apply_traffic(apply_setting)
     gpu_launches = int(nl_prof.sum())
     shares = {name: round(float(ms_prof[k]) / max(1e-9, float(ms_prof.sum())), 4)
               for k, name in enumerate(["validate", "group", "apply", "recover", "query", "sort"])}
+    C.cupc_destroy(g)
+    del E, O, Eflat
+    torch.cuda.empty_cache()
 
     cpu = None
-    if rank == 0 and not args.no_cpu_baseline:
-        n, dt, tq = oracle_sample(E)
-        cpu = {"value": n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"first {n} inserts of the dense stream + one 1k-pair Connected batch + spanning "
-                         "forest (single thread)",
-               "query_batch_ms": 1e3 * tq}
+    if rank == 0 and world == 1:
+        dense_E, dense_D = make_dense_stream()
+        rows["dense_v16384"], extra["batch_size_vs_query_latency"] = dense_rows(torch, C, dev, stream, dense_E,
+                                                                                dense_D)
+        plain_steps = WL.plain_stream(V=1024, seed=1)
+        rows["plain_v1024"] = plain_rows(torch, C, dev, stream, plain_steps)
+        cl, border, cpairs, comp = WL.clique_stream(V=131072, seed=7)
+        rows["cliques_v131072"] = clique_rows(torch, C, dev, stream, cl, border, cpairs, comp)
+        streams = WL.serving_streams(n_graphs=64, upd_range=(5e4, 5e5), seed=5)
+        if not args.no_serving:
+            rows["serving_64_graphs"] = serving_rows(torch, C, streams)
+        if not args.no_batching:
+            extra["batching_many_graphs"] = many_graphs(torch, C, dev, stream)
+            extra["paper_stream_shape"] = paper_stream(torch, C, dev, stream)
+        if not args.no_cpu_baseline:
+            cs = cpu_samples(E_cpu_sample, dense_E, plain_steps, cl, border[0][0], streams[0])
+            for k, v in cs.items():
+                rows.setdefault(k, {})["cpu_oracle_1_thread"] = v
+            cpu = {"value": cs["rmat_v131072"]["updates_per_s"], "unit": UNIT, "cores": 1, "kind": "oracle",
+                   "sample": f"first {CPU_RMAT_SAMPLE} updates of the headline stream + one 1k-pair "
+                             "Connected batch + spanning forest (single thread)",
+                   "query_batch_ms": cs["rmat_v131072"]["query_batch_ms"]}
 
     if rank == 0:
+        cfg = headline_config(n, nb, sizes)
+        cfg["apply_tuning_buckets_set"] = n_buckets
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-                "config": workload_config(nE, nD),
+                "config": cfg,
                 "e2e": {"value": e2e_val, "unit": UNIT,
-                        "h2d_bytes_per_step": int(9 * (nE + nD)), "d2h_bytes_per_step": int(8 * nf_h)},
+                        "h2d_bytes_per_step": int(9 * n + 8000), "d2h_bytes_per_step": int(1000 + 8 * nf_h)},
                 "gpu_launches": gpu_launches,
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                             "frac": achieved / peak, "traffic": traffic,
+                             "frac": achieved / peak, "traffic": apply_traffic("rmat_v131072"),
                              "kernel": "k_apply", "algorithmic_bytes_per_launch": apply_bytes_per_launch,
-                             "dense_sweep_bytes_per_launch": sweep_bytes_per_launch,
-                             "edges_per_launch": BATCH, "avg_launch_ms": apply_ms,
-                             "apply_setting": apply_setting,
-                             "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst copy)" if peaks else "fallback"},
+                             "dense_sweep_bytes_per_launch": float(np.mean(sweep)),
+                             "launches_per_step": len(touched), "avg_launch_ms": apply_ms,
+                             "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst copy), of measured" if peaks
+                             else "fallback 6800 GB/s"},
                 "kernel_time_share": shares,
-                "batch_size_vs_query_latency": sweep,
-                "paper_stream_shape": pstream,
-                "query_latency_us": {"dense_after_batch_p50": statistics.median(lat_dense),
-                                     "dense_after_batch_p99": float(np.percentile(lat_dense, 99)),
-                                     **plain},
-                "forest_edges": int(nf),
-                "batching": batching,
-                "serving": serving,
+                "per_config": rows,
+                **extra,
                 "cpu_baseline": cpu, "clocks": clk}
         print(json.dumps(line), flush=True)
     if pg is not None:
         pg.destroy_process_group()
 
 
-def batching_compare(torch, C, dev, stream, n_batches=48, rounds=30):
-    """Batched vs one-batch-per-launch (device-resident inputs, CUDA events).
+# ---- the other workloads (rank 0, one GPU) -------------------------------------
 
-    uneven: R-MAT stream on V = 2^17 (a=.57, b=c=.19, d=.05, 20% deletes of
-    present edges, batch sizes log-uniform in [1k, 4M]), the first n_batches
-    batches: one cupc_update_batch per batch vs cupc_update_batches over the
-    back-to-back batches. many_graphs: 64 graphs with V log-uniform in
-    [2^10, 2^15], each receiving a 1k-edge batch per round: 64
-    cupc_update_batch calls per round vs one cupc_batcher_update call (CUDA
-    graph replay, and without the graph)."""
-    from paper_2509_14433_gb300 import autotune as AT
-    out = {}
-    # -- uneven batches of one graph
-    s = WL.RmatStream(levels=17, seed=3, device=dev)
-    bl = [s.next_batch() for _ in range(n_batches)]
-    sizes = [len(b[1]) for b in bl]
-    E = torch.cat([b[0].reshape(-1) for b in bl]).contiguous()
-    O = torch.cat([b[1] for b in bl]).contiguous()
-    offs = np.cumsum([0] + sizes).astype(np.uint64)
-    del bl, s
-    torch.cuda.empty_cache()
-    V = 1 << 17
-    st, g = C.cupc_init(V, 1, (0, 0, 0, 4 << 20), None, stream)
+def dense_rows(torch, C, dev, stream, E, D):
+    """Dense V=16384: the whole job (all inserts, 10% deletes in 2^20
+    batches, the forest), the query latency after a 2^20-edge batch, and the
+    batch size against the latency of the next query batch."""
+    V = V_DENSE
+    nE, nD = len(E), len(D)
+    E_d = torch.from_numpy(E.reshape(-1)).to(dev)
+    D_d = torch.from_numpy(D.reshape(-1)).to(dev)
+    ins_d = torch.ones(nE, dtype=torch.int8, device=dev)
+    del_d = torch.full((nD,), -1, dtype=torch.int8, device=dev)
+    forest_d = torch.empty(V, dtype=torch.int64, device=dev)
+    st, g = C.cupc_init(V, SEED, None, None, stream)
     C.check(st)
-    AT.apply_buckets(g, V)  # each batch with the setting of its size
+    from paper_2509_14433_gb300 import autotune as AT
+    AT.apply_buckets(g, V)
 
-    def plain():
-        for i in range(n_batches):
-            C.check(C.cupc_update_batch(g, E.data_ptr() + 8 * int(offs[i]), O.data_ptr() + int(offs[i]),
-                                        sizes[i], stream))
+    def job():
+        C.check(C.cupc_reset(g, stream))
+        for i in range(0, nE, BATCH):
+            C.check(C.cupc_update_batch(g, E_d[2 * i:], ins_d[i:], min(BATCH, nE - i), stream))
+        for i in range(0, nD, BATCH):
+            C.check(C.cupc_update_batch(g, D_d[2 * i:], del_d[i:], min(BATCH, nD - i), stream))
+        st, nf = C.cupc_spanning_forest(g, forest_d, V, stream)
+        C.check(st, ok=(C.CUPC_OK, C.CUPC_EINCOMPLETE))
+        return nf
 
-    def coalesced():
-        C.check(C.cupc_update_batches(g, E, O, offs, n_batches, stream))
-
-    res = {}
-    for name, fn in (("one_batch_per_launch", plain), ("coalesced", coalesced)):
-        C.cupc_reset(g, stream)
-        fn()
-        C.cupc_reset(g, stream)
+    job()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(2):
+        nf = job()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    upd_s = 2 * (nE + nD) / (e0.elapsed_time(e1) / 1e3)
+    pairs = torch.from_numpy(WL.uniform_pairs(V, 1000, WL.rng(77), distinct=False).reshape(-1)).to(dev)
+    q_out = torch.empty(1000, dtype=torch.uint8, device=dev)
+    lat = []
+    for k in range(QUERY_SAMPLES + 5):
+        i = (k % 6) * BATCH  # toggle one 2^20-edge batch, then ask
+        C.check(C.cupc_update_batch(g, E_d[2 * i:], ins_d[i:], BATCH, stream))
         torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        fn()
-        e1.record(stream)
+        t = time.perf_counter()
+        C.check(C.cupc_query(g, pairs, 1000, q_out, stream))
         torch.cuda.synchronize()
-        res[name] = int(offs[-1]) / (e0.elapsed_time(e1) / 1e3)
+        if k >= 5:
+            lat.append((time.perf_counter() - t) * 1e6)
+    C.check(C.cupc_sync(g, stream))
+    job()  # back to the stream's final graph (a valid stream for the sweep)
+    sweep = batch_latency_sweep(torch, C, g, D_d, ins_d, del_d, pairs, q_out, stream)
     C.cupc_destroy(g)
-    del E, O
-    torch.cuda.empty_cache()
-    out["uneven_rmat_v131072"] = {"updates": int(offs[-1]), "batches": n_batches,
-                                  "batch_min": int(min(sizes)), "batch_max": int(max(sizes)),
-                                  "updates_per_s": res}
-    # -- many graphs, one small batch each per round
+    row = {"updates_per_s": upd_s, "updates_per_step": nE + nD, "forest_edges": int(nf),
+           "query_after_2^20_batch": pcts(lat), "queries_per_s_in_query_batches": 1000 / (np.mean(lat) * 1e-6)}
+    return row, sweep
+
+
+def batch_latency_sweep(torch, C, g, D_d, ins_d, del_d, p_d, q_out, stream, reps=200):
+    """Update batch size against the latency of the next Connected query
+    batch (the trade-off the paper's update buffering makes): for each size
+    b from 1 to 4M, insert then delete the first b of the deleted edges
+    (absent, then present: a valid stream) and ask 1k pairs after each batch,
+    `reps` times. Latency = host submit of the batch to the query's answer,
+    recovery included."""
+    out = {}
+    for b in [4 ** k for k in range(12)]:
+        upd, lat = [], []
+        for k in range(reps + 2):  # the first two passes warm up
+            ops = ins_d if k % 2 == 0 else del_d
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            C.check(C.cupc_update_batch(g, D_d, ops, b, stream))
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            C.check(C.cupc_query(g, p_d, 1000, q_out, stream))
+            torch.cuda.synchronize()
+            t2 = time.perf_counter()
+            if k >= 2:
+                upd.append(t1 - t0)
+                lat.append((t2 - t0) * 1e6)
+        out[str(b)] = {"updates_per_s": b / statistics.median(upd), **pcts(lat)}
+    return out
+
+
+def plain_rows(torch, C, dev, stream, steps, reps=50):
+    """Plain V=1024: ER(0.5) start graph + 200k toggles, a 1k-pair Connected
+    batch every 10k updates, replayed `reps` times (20 query batches each):
+    toggle updates/s and query latency (host submit -> answers ready,
+    recovery included), with and without incremental labels."""
+    V = 1024
+    out = {}
+    dsteps = []
+    for s in steps:
+        if s[0] == "update":
+            dsteps.append(("u", torch.from_numpy(s[1].reshape(-1)).to(dev), torch.from_numpy(s[2]).to(dev), len(s[2])))
+        else:
+            dsteps.append(("q", torch.from_numpy(s[1].reshape(-1)).to(dev),
+                           torch.empty(len(s[1]), dtype=torch.uint8, device=dev), len(s[1])))
+    for mode, inc in (("recovery_per_query", 0), ("incremental_labels", 1)):
+        st, g = C.cupc_init(V, SEED, None, None, stream)
+        C.check(st)
+        C.check(C.cupc_set_incremental(g, inc, stream))
+        lat, upd_t, n_upd = [], 0.0, 0
+        for rep in range(reps + 1):
+            C.cupc_reset(g, stream)
+            for kind, a, b, n in dsteps:
+                torch.cuda.synchronize()
+                t = time.perf_counter()
+                if kind == "u":
+                    C.check(C.cupc_update_batch(g, a, b, n, stream))
+                else:
+                    C.check(C.cupc_query(g, a, n, b, stream))
+                torch.cuda.synchronize()
+                dt = time.perf_counter() - t
+                if rep == 0:
+                    continue  # warm-up pass
+                if kind == "u":
+                    if n <= 10_000:
+                        upd_t += dt
+                        n_upd += n
+                else:
+                    lat.append(dt * 1e6)
+        C.cupc_destroy(g)
+        out[mode] = {"toggle_updates_per_s": n_upd / upd_t, "query": pcts(lat),
+                     "queries_per_s_in_query_batches": 1000 / (np.mean(lat) * 1e-6)}
+    return out
+
+
+def clique_rows(torch, C, dev, stream, cl, order, pr, comp, rounds=63):
+    """Adversarial V=131072: 256 cliques of 512 (33.5M edges, inserted in
+    2^20 batches: the set-up, timed on its own), then `rounds` passes of 8
+    bridge insert batches and 8 shuffled bridge delete batches of 64k, a
+    1k-pair Connected batch after every batch (half inside one clique, half
+    across two). Answers are checked against the exact components."""
+    V, k = 131072, 256
+    st, g = C.cupc_init(V, SEED, (0, 0, 0, BATCH), None, stream)
+    C.check(st)
+    from paper_2509_14433_gb300 import autotune as AT
+    AT.apply_buckets(g, V)
+    cl_d = torch.from_numpy(cl.reshape(-1)).to(dev)
+    ones = torch.ones(len(cl), dtype=torch.int8, device=dev)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for i in range(0, len(cl), BATCH):
+        C.check(C.cupc_update_batch(g, cl_d[2 * i:], ones[i:], min(BATCH, len(cl) - i), stream))
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t
+    dorder = [(torch.from_numpy(np.ascontiguousarray(E).reshape(-1)).to(dev),
+               torch.full((len(E),), op, dtype=torch.int8, device=dev), len(E)) for E, op in order]
+    P_d = torch.from_numpy(pr.reshape(-1)).to(dev)
+    q_out = torch.empty(1000, dtype=torch.uint8, device=dev)
+    # the exact answers after each batch of a pass: cliques joined by the
+    # bridges present
+    want = []
+    present = np.zeros(0, np.int64)
+    for E, op in order:
+        ids = E[:, 0].astype(np.int64) * V + E[:, 1]
+        present = np.union1d(present, ids) if op == 1 else np.setdiff1d(present, ids)
+        parent = np.arange(k)
+
+        def find(x):
+            while parent[x] != x:
+                parent[x] = parent[parent[x]]
+                x = parent[x]
+            return x
+
+        for x, y in zip(comp[present // V].tolist(), comp[present % V].tolist()):
+            rx, ry = find(x), find(y)
+            if rx != ry:
+                parent[rx] = ry
+        root = np.array([find(c) for c in range(k)])
+        want.append(root[comp[pr[:, 0]]] == root[comp[pr[:, 1]]])
+    lat, upd_t, n_upd, wrong = [], 0.0, 0, 0
+    for rnd in range(rounds + 1):
+        for j, (e, o, m) in enumerate(dorder):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            C.check(C.cupc_update_batch(g, e, o, m, stream))
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            C.check(C.cupc_query(g, P_d, 1000, q_out, stream))
+            torch.cuda.synchronize()
+            t2 = time.perf_counter()
+            if rnd:
+                upd_t += t1 - t0
+                n_upd += m
+                lat.append((t2 - t1) * 1e6)
+                wrong += int((q_out.cpu().numpy().astype(bool) != want[j]).sum())
+    C.cupc_destroy(g)
+    return {"clique_setup_updates_per_s": len(cl) / setup_s, "bridge_updates_per_s": n_upd / upd_t,
+            "query_after_each_bridge_batch": pcts(lat), "wrong_answers": wrong,
+            "queries_per_s_in_query_batches": 1000 / (np.mean(lat) * 1e-6)}
+
+
+def many_graphs(torch, C, dev, stream, rounds=30):
+    """64 graphs with V log-uniform in [2^10, 2^15], each receiving a
+    1k-edge batch per round: 64 cupc_update_batch calls per round vs one
+    cupc_batcher_update call (CUDA graph replay, and without the graph)."""
     rng = WL.rng(17)
     Vs = [int(2 ** x) for x in rng.uniform(10, 15, size=64)]
     graphs = []
@@ -497,99 +796,153 @@ def batching_compare(torch, C, dev, stream, n_batches=48, rounds=30):
             C.cupc_batcher_destroy(b)
     for h in graphs:
         C.cupc_destroy(h)
-    out["many_graphs_64x1k"] = {"graphs": len(graphs), "V_min": min(Vs), "V_max": max(Vs), "rounds": rounds,
-                                "updates_per_s": res}
-    return out
+    return {"graphs": len(graphs), "V_min": min(Vs), "V_max": max(Vs), "rounds": rounds, "updates_per_s": res}
 
 
-def serving_compare(torch, C, dev, n_graphs=64, upd_range=(5e4, 5e5), seed=5):
-    """Serving workload (64 graphs, V log-uniform in [2^10, 2^15], ER(p)
-    insert/delete streams, p ~ U[0.1, 0.9], batches log-uniform in [1k, 1M],
-    a 1k-pair Connected batch after every 100k updates of a graph; each
-    graph's stream has log-uniform[upd_range] updates). All requests arrive
-    at once, round-robin over graphs. served: cupc_server (continuous
-    batching, multi-graph launches, overlapped query streams) with no memory
-    cap and with a cap of 25% of the graphs' total workspace (graphs wait for
-    admission and close when done); plain: one thread, one request at a time
-    through cupc_update_batch / cupc_query, each finished before the next.
-    Latency = arrival to completion; updates/s = all updates / makespan."""
-    streams = WL.serving_streams(n_graphs=n_graphs, upd_range=upd_range, seed=seed)
+def wait_until(due):
+    while True:
+        now = time.perf_counter()
+        if now >= due:
+            return
+        if due - now > 2e-4:
+            time.sleep(due - now - 1e-4)
+
+
+def serving_rows(torch, C, streams, maxb=1 << 20):
+    """Serving workload: 64 graphs, V log-uniform in [2^10, 2^15], ER(p)
+    insert/delete streams with p ~ U[0.1, 0.9], batches log-uniform in
+    [1k, 1M], a 1k-pair Connected batch after every 100k updates of a graph;
+    requests in round-robin order over the graphs.
+
+    closed loop: every request submitted at t = 0; cupc_server with no memory
+    cap and with a cap of 25% of the graphs' total workspace, against one
+    thread serving one request at a time. Latency = arrival to completion.
+
+    open loop: requests arrive with seeded exponential gaps at a fixed
+    offered rate (a fraction of the one-at-a-time arm's closed-loop request
+    rate, so below its saturation), replayed until at least 1000 query
+    batches were measured per point; latency is measured from each request's
+    scheduled arrival, for cupc_server and for the one-at-a-time arm (a FIFO
+    single server: a request starts at max(its arrival, the previous
+    completion))."""
     order = WL.round_robin(streams)
     total_upd = sum(st[3] for st in streams)
-    maxb = 1 << 20
+    n_graphs = len(streams)
     ws = [C.cupc_workspace_bytes(st[0], (0, 0, 0, maxb)) for st in streams]
-    out = {"graphs": n_graphs, "updates": int(total_upd), "requests": len(order),
-           "queries": sum(1 for _, s_ in order if s_[0] == "query")}
+    reqs = []
+    for i, stp in order:
+        if stp[0] == "update":
+            reqs.append((i, "u", np.ascontiguousarray(stp[1], np.uint32), np.ascontiguousarray(stp[2], np.int8)))
+        else:
+            reqs.append((i, "q", np.ascontiguousarray(stp[1], np.uint32), None))
+    nq = sum(1 for r in reqs if r[1] == "q")
+    out = {"graphs": n_graphs, "updates": int(total_upd), "requests": len(reqs), "query_batches": nq}
+    last = {}
+    for k, r in enumerate(reqs):
+        last[r[0]] = k
 
-    def served(cap_bytes):
-        st, srv = C.cupc_server_create(int(cap_bytes), n_graphs, maxb, 4)
+    def served_run(cap_bytes, arrivals=None):
+        """One pass of every request through a fresh server; arrivals: the
+        scheduled arrival offsets (s) or None (all at t = 0). Returns
+        (query latencies from arrival in us, makespan s, stats)."""
+        st, srv = C.cupc_server_create(int(cap_bytes), n_graphs, maxb, 4, 1 << 30)
         C.check(st)
         try:
             ids = [C.cupc_server_open(srv, s_[0], s_[1])[1] for s_ in streams]
-            last = {}
-            for k, (i, _) in enumerate(order):
-                last[i] = k
-            keep, qt, ut = [], [], []
+            outs, ut, qt = [], [], []
             t0 = time.perf_counter()
-            for k, (i, stp) in enumerate(order):
-                if stp[0] == "update":
-                    e = np.ascontiguousarray(stp[1], np.uint32)
-                    o = np.ascontiguousarray(stp[2], np.int8)
-                    keep.append((e, o))
-                    r, t = C.cupc_server_update(srv, ids[i], e, o, len(o))
+            for k, (i, kind, a, b) in enumerate(reqs):
+                lag = 0.0
+                if arrivals is not None:
+                    wait_until(t0 + arrivals[k])
+                    lag = time.perf_counter() - (t0 + arrivals[k])
+                if kind == "u":
+                    r, t = C.cupc_server_update(srv, ids[i], a, b, len(b))
                     ut.append(t)
                 else:
-                    p = np.ascontiguousarray(stp[1], np.uint32)
-                    ans = np.zeros(len(p), np.uint8)
-                    keep.append((p, ans))
-                    r, t = C.cupc_server_query(srv, ids[i], p, len(p), ans)
-                    qt.append(t)
+                    ans = np.zeros(len(a), np.uint8)
+                    outs.append(ans)
+                    r, t = C.cupc_server_query(srv, ids[i], a, len(a), ans)
+                    qt.append((t, lag))
                 C.check(r, "submit")
                 if k == last[i]:
                     ut.append(C.cupc_server_close(srv, ids[i])[1])
-            lat = []
             for t in ut:
                 C.check(C.cupc_server_wait(srv, t, 600000)[0], "update")
-            for t in qt:
+            lat = []
+            for t, lag in qt:
                 r, l_us = C.cupc_server_wait(srv, t, 600000)
                 C.check(r, "query")
-                lat.append(l_us)
+                lat.append(l_us + 1e6 * lag)
             span = time.perf_counter() - t0
             stats = np.zeros(8, np.uint64)
             C.cupc_server_stats(srv, stats)
-            return {"updates_per_s": total_upd / span, "query_p50_us": float(np.percentile(lat, 50)),
-                    "query_p99_us": float(np.percentile(lat, 99)), "makespan_s": span,
-                    "update_launches": int(stats[2]), "update_requests": int(stats[3]),
-                    "admission_waits": int(stats[5])}
+            return lat, span, stats
         finally:
             C.cupc_server_destroy(srv)
 
-    out["served_no_cap"] = served(sum(ws) * 1.02 + (256 << 20))
-    out["served_cap_25pct"] = served(0.25 * sum(ws))
-    # plain: one request at a time on the caller's thread
     graphs = []
     for s_ in streams:
         r, g = C.cupc_init(s_[0], s_[1], (0, 0, 0, maxb), None, None)
         C.check(r)
         graphs.append(g)
-    try:
+
+    def plain_run(arrivals=None):
+        """One thread, one request at a time, each finished before the next
+        starts (FIFO); latency from the scheduled arrival."""
+        for g in graphs:
+            C.cupc_reset(g, None)
+        torch.cuda.synchronize()
         lat = []
         t0 = time.perf_counter()
-        for i, stp in order:
-            if stp[0] == "update":
-                e = np.ascontiguousarray(stp[1], np.uint32)
-                o = np.ascontiguousarray(stp[2], np.int8)
-                C.check(C.cupc_update_batch(graphs[i], e, o, len(o), None))
+        for k, (i, kind, a, b) in enumerate(reqs):
+            arr = 0.0 if arrivals is None else arrivals[k]
+            if arrivals is not None:
+                wait_until(t0 + arr)
+            if kind == "u":
+                C.check(C.cupc_update_batch(graphs[i], a, b, len(b), None))
                 torch.cuda.synchronize()
             else:
-                p = np.ascontiguousarray(stp[1], np.uint32)
-                ans = np.zeros(len(p), np.uint8)
-                C.check(C.cupc_query(graphs[i], p, len(p), ans, None))
-                lat.append((time.perf_counter() - t0) * 1e6)
-        span = time.perf_counter() - t0
-        out["one_request_at_a_time"] = {"updates_per_s": total_upd / span,
-                                        "query_p50_us": float(np.percentile(lat, 50)),
-                                        "query_p99_us": float(np.percentile(lat, 99)), "makespan_s": span}
+                ans = np.zeros(len(a), np.uint8)
+                C.check(C.cupc_query(graphs[i], a, len(a), ans, None))
+                lat.append((time.perf_counter() - (t0 + arr)) * 1e6)
+        return lat, time.perf_counter() - t0
+
+    try:
+        full = sum(ws) * 1.02 + (256 << 20)
+        out["closed_loop"] = {}
+        for name, cap in (("served_no_cap", full), ("served_cap_25pct", 0.25 * sum(ws))):
+            served_run(cap)  # warm-up
+            lat, span, stats = served_run(cap)
+            out["closed_loop"][name] = {
+                "updates_per_s": total_upd / span, "query": pcts(lat), "makespan_s": span,
+                "update_launches": int(stats[2]), "update_requests": int(stats[3]),
+                "admission_waits": int(stats[5])}
+        plain_run()  # warm-up
+        lat, span = plain_run()
+        out["closed_loop"]["one_request_at_a_time"] = {"updates_per_s": total_upd / span, "query": pcts(lat),
+                                                       "makespan_s": span}
+        rate_plain = len(reqs) / span  # requests/s the one-at-a-time arm sustains
+        rounds = max(1, -(-QUERY_SAMPLES // nq))
+        g_rng = WL.rng(31)
+        pts = []
+        for frac in (0.25, 0.5, 0.75):
+            rate = frac * rate_plain
+            pt = {"offered_requests_per_s": rate, "offered_updates_per_s": rate * total_upd / len(reqs),
+                  "fraction_of_one_at_a_time_capacity": frac}
+            for arm in ("served", "one_request_at_a_time"):
+                lat_all, upd_s = [], []
+                for _ in range(rounds):
+                    arrivals = np.cumsum(g_rng.exponential(1.0 / rate, size=len(reqs)))
+                    if arm == "served":
+                        lat, span, _ = served_run(full, arrivals)
+                    else:
+                        lat, span = plain_run(arrivals)
+                    lat_all += lat
+                    upd_s.append(total_upd / span)
+                pt[arm] = {"query": pcts(lat_all), "achieved_updates_per_s": float(np.mean(upd_s))}
+            pts.append(pt)
+        out["open_loop"] = pts
     finally:
         for g in graphs:
             C.cupc_destroy(g)
@@ -606,7 +959,7 @@ def paper_stream(torch, C, dev, stream):
     uniform Connected pairs (10% of the operations are queries). Each whole
     stream runs with a full recovery per query burst and with incremental
     labels (cupc_set_incremental): updates/s and queries/s over the stream,
-    the recoveries it ran, and the latency of every 25th burst (its update
+    the recoveries it ran, and the latency of every 16th burst (its update
     batch and its queries, host submit -> answers ready)."""
     V = 1 << 13
     paper = {"standard": ("K13", 1.79e6, 3.37e6), "fixed_forest": ("K13-FF", 4.56e6, 6.92e6)}
@@ -669,87 +1022,14 @@ def paper_stream(torch, C, dev, stream):
             dt = time.perf_counter() - t0
             nrec = recoveries() - r0
             C.check(C.cupc_reset(g, stream))
-            lat = run(bursts, sample_every=25)
+            lat = run(bursts, sample_every=16)
             out[mode] = {"updates_per_s": len(E) / dt, "queries_per_s": n_q / dt, "recoveries": nrec,
-                         "burst_latency_p50_us": statistics.median(lat),
-                         "burst_latency_p99_us": float(np.percentile(lat, 99))}
+                         "burst_latency": pcts(lat)}
         res[shape] = out
         del E_d, ops_d, P_d, out_d
     C.check(C.cupc_sync(g, stream), "paper stream", ok=(C.CUPC_OK, C.CUPC_EINCOMPLETE))
     C.cupc_destroy(g)
     return res
-
-
-def plain_stream_latency(torch, C, dev, stream, inc=0):
-    """V=1024 ER(0.5) start graph + 200k toggles, a 1k-pair Connected batch
-    every 10k updates: updates/s over the toggles, query latency p50/p99
-    (host submit -> answers ready, recovery included). inc: incremental
-    labels (the stream is valid: a toggle inserts an absent edge or deletes
-    a present one)."""
-    V = 1024
-    steps = WL.plain_stream(V=V, seed=1)
-    st, g = C.cupc_init(V, 1, None, None, stream)
-    C.check(st)
-    C.check(C.cupc_set_incremental(g, inc, stream))
-    dsteps = []
-    for s in steps:
-        if s[0] == "update":
-            dsteps.append(("u", torch.from_numpy(s[1].reshape(-1)).to(dev), torch.from_numpy(s[2]).to(dev), len(s[2])))
-        else:
-            dsteps.append(("q", torch.from_numpy(s[1].reshape(-1)).to(dev), torch.empty(len(s[1]), dtype=torch.uint8,
-                                                                                       device=dev), len(s[1])))
-    lat, upd_t, n_upd = [], 0.0, 0
-    for rep in range(3):
-        C.cupc_reset(g, stream)
-        for kind, a, b, n in dsteps:
-            torch.cuda.synchronize()
-            t = time.perf_counter()
-            if kind == "u":
-                C.check(C.cupc_update_batch(g, a, b, n, stream))
-            else:
-                C.check(C.cupc_query(g, a, n, b, stream))
-            torch.cuda.synchronize()
-            dt = time.perf_counter() - t
-            if rep == 0:
-                continue  # warm-up pass
-            if kind == "u":
-                if n <= 10_000:
-                    upd_t += dt
-                    n_upd += n
-            else:
-                lat.append(dt * 1e6)
-    C.cupc_destroy(g)
-    sfx = "_incremental" if inc else ""
-    return {f"plain_v1024{sfx}_p50": statistics.median(lat), f"plain_v1024{sfx}_p99": float(np.percentile(lat, 99)),
-            f"plain_v1024{sfx}_toggle_updates_per_s": n_upd / upd_t, f"plain_v1024{sfx}_queries": len(lat)}
-
-
-def batch_latency_sweep(torch, C, g, D_d, ins_d, del_d, p_d, q_out, stream):
-    """Update batch size against the latency of the next Connected query
-    batch (the trade-off the paper's update buffering makes): for each size
-    b, insert then delete the first b of the deleted edges (absent, then
-    present: a valid stream) and ask 1k pairs after each batch. Latency =
-    host submit of the batch to the query's answer, recovery included."""
-    out = {}
-    for b in (1 << 10, 1 << 14, 1 << 17, 1 << 20, 1 << 22):
-        upd, lat = [], []
-        for k in range(9):  # the first pass warms up
-            ops = ins_d if k % 2 == 0 else del_d
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            C.check(C.cupc_update_batch(g, D_d, ops, b, stream))
-            torch.cuda.synchronize()
-            t1 = time.perf_counter()
-            C.check(C.cupc_query(g, p_d, 1000, q_out, stream))
-            torch.cuda.synchronize()
-            t2 = time.perf_counter()
-            if k:
-                upd.append(t1 - t0)
-                lat.append((t2 - t0) * 1e6)
-        C.check(C.cupc_update_batch(g, D_d, del_d, b, stream))  # the last pass inserted: leave the graph as it was
-        out[str(b)] = {"updates_per_s": b / statistics.median(upd), "query_p50_us": statistics.median(lat),
-                       "query_p99_us": float(np.percentile(lat, 99))}
-    return out
 
 
 def run_apply_profile(args):
@@ -761,11 +1041,11 @@ def run_apply_profile(args):
 
     from paper_2509_14433_gb300 import cupc as C
     torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
     if args.profile_case == "rmat":
         V = 1 << 15
         s = WL.RmatStream(levels=15, seed=3, batch_lo=1 << 20, batch_hi=4 << 20, device="cuda")
         bl = [s.next_batch() for _ in range(6)]
-        stream = torch.cuda.current_stream()
         st, g = C.cupc_init(V, SEED, (0, 0, 0, 4 << 20), None, stream)
         C.check(st)
         for e, o in bl:
@@ -778,11 +1058,10 @@ def run_apply_profile(args):
     n = 8 * BATCH
     E_d = torch.from_numpy(E[:n].reshape(-1)).cuda()
     ins_d = torch.ones(n, dtype=torch.int8, device="cuda")
-    stream = torch.cuda.current_stream()
     st, g = C.cupc_init(V_DENSE, SEED, None, None, stream)
     C.check(st)
     from paper_2509_14433_gb300 import autotune as AT
-    AT.apply(g, V_DENSE, BATCH)  # the bench's apply setting
+    AT.apply(g, V_DENSE, BATCH)  # the tuned apply setting of this batch size
     for i in range(0, n, BATCH):
         C.check(C.cupc_update_batch(g, E_d[2 * i:], ins_d[i:], BATCH, stream))
     pairs = torch.from_numpy(WL.uniform_pairs(V_DENSE, 1000, WL.rng(5)).reshape(-1)).cuda()

@@ -51,10 +51,11 @@ constexpr uint32_t kPlanGridCap = 8192;
 // every layer of kStage records sit in shared memory.
 constexpr uint32_t kStage = 64;
 // Dynamic shared memory of an apply CTA for graphs of at most L layers:
-// rows x threads fold rows, kStage staged records with their L checksums,
-// the L layer checksum keys and the records' vertices (direct path).
+// rows x threads fold rows, two buffers of kStage staged records, the L
+// checksums of one pass, the L layer checksum keys and two buffers of the
+// records' vertices (direct path).
 inline size_t apply_smem_bytes(uint32_t rows, uint32_t threads, uint32_t L) {
-  return (size_t)rows * threads * 16 + (size_t)kStage * 8 * (1 + L) + (size_t)L * 8 + (size_t)kStage * 4;
+  return (size_t)rows * threads * 16 + (size_t)kStage * 8 * (2 + L) + (size_t)L * 8 + (size_t)kStage * 2 * 4;
 }
 // Key words of a graph: L*(C+1) (column multipliers and layer checksum
 // keys) + 3*L*C (the other multiply-add-shift words of every column).

@@ -132,10 +132,6 @@ __device__ __forceinline__ void xor_bucket_atomic(ulonglong2* p, ulonglong2 v) {
   atomicXor(&p->y, v.y);
 }
 
-__device__ __forceinline__ void prefetch_l2(const void* p) {
-  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
-}
-
 // What one thread of the apply kernel does for a graph: tid = r*P + s; r < L
 // is the layer, s < C a column, s == C the deterministic bucket. Lanes past
 // the layout are idle: they fold into their own row 0, which is never
@@ -208,20 +204,21 @@ __device__ __forceinline__ uint32_t lane_depth(const ApplyLane& l, uint64_t x) {
 }
 
 // Shared memory of an apply CTA: fold rows (rows x threads buckets), then
-// the staged records, their per-layer checksums, the layer checksum keys
-// and the records' vertices (direct path).
+// the staged records (two buffers: a pass writes one while the previous
+// pass may still be read from the other), their per-layer checksums, the
+// layer checksum keys and the records' vertices (direct path, two buffers).
 struct ApplySmem {
   ulonglong2* rows;
-  uint64_t* x;     // kStage
+  uint64_t* x;     // 2 * kStage
   uint64_t* g;     // kStage * L, [record][layer]
   uint64_t* kchk;  // L
-  uint32_t* w;     // kStage
+  uint32_t* w;     // 2 * kStage
 };
 __device__ __forceinline__ ApplySmem apply_smem(unsigned char* raw, uint32_t rows, uint32_t L) {
   ApplySmem m;
   m.rows = reinterpret_cast<ulonglong2*>(raw);
   m.x = reinterpret_cast<uint64_t*>(m.rows + (size_t)rows * blockDim.x);
-  m.g = m.x + kStage;
+  m.g = m.x + 2 * kStage;
   m.kchk = m.g + (size_t)kStage * L;
   m.w = reinterpret_cast<uint32_t*>(m.kchk + L);
   return m;
@@ -233,20 +230,29 @@ __device__ __forceinline__ void load_kchk(const ApplySmem& m, const uint64_t* ke
   for (uint32_t r = threadIdx.x; r < L; r += blockDim.x) m.kchk[r] = keys[r * (C + 1) + C];
 }
 
-// Stage records rec[0..n), n <= kStage: idx, and G_r(idx) for every layer,
-// computed once per (record, layer) and shared by the layer's lanes.
-__device__ __forceinline__ void stage_records(const ApplyLane& l, const ApplySmem& m,
-                                              const uint64_t* __restrict__ rec, const uint32_t* __restrict__ recw,
-                                              uint32_t n, uint32_t L) {
-  const uint32_t total = n * L;
+// Records staged per pass by a CTA of blockDim.x threads: one record per
+// thread, at most kStage.
+__device__ __forceinline__ uint32_t stage_size() { return min(kStage, (uint32_t)blockDim.x); }
+
+// Stage one pass of nc <= stage_size() records whose indices are in xr
+// (thread t holds record t) into record buffer `buf` (0 or 1; consecutive
+// passes alternate): idx, and G_r(idx) for every layer, computed once per
+// (record, layer) and shared by the layer's lanes. The caller has already
+// loaded xr (and w, for the direct path) from global memory. Returns the
+// staged records.
+__device__ __forceinline__ const uint64_t* stage_pass(const ApplyLane& l, const ApplySmem& m, uint64_t xr,
+                                                      uint32_t wr, bool with_w, uint32_t nc, uint32_t L,
+                                                      uint32_t buf) {
+  uint64_t* xs = m.x + buf * kStage;
+  if (threadIdx.x < nc) {
+    xs[threadIdx.x] = xr;
+    if (with_w) m.w[buf * kStage + threadIdx.x] = wr;
+  }
+  __syncthreads();  // the records are in; every lane is done with the previous pass
+  const uint32_t total = nc * L;
   uint32_t i = l.si0, r = l.sr0;
   for (uint32_t k = threadIdx.x; k < total; k += blockDim.x) {
-    const uint64_t x = __ldg(rec + i);
-    if (r == 0) {
-      m.x[i] = x;
-      if (recw) m.w[i] = __ldg(recw + i);
-    }
-    m.g[k] = mix64(x ^ m.kchk[r]);
+    m.g[k] = mix64(xs[i] ^ m.kchk[r]);
     i += l.sqi;
     r += l.sqr;
     if (r >= L) {
@@ -255,6 +261,7 @@ __device__ __forceinline__ void stage_records(const ApplyLane& l, const ApplySme
     }
   }
   __syncthreads();
+  return xs;
 }
 
 __device__ __forceinline__ void fold_record(ulonglong2* gb, ulonglong2* my_rows, uint32_t rs, uint32_t R, uint32_t d,
@@ -269,32 +276,52 @@ __device__ __forceinline__ void fold_record(ulonglong2* gb, ulonglong2* my_rows,
   }
 }
 
+// Two records into one lane's rows with both rows read before either is
+// written, so the two read-modify-writes overlap instead of forming a chain.
+// When both land in one row, the later store carries both records.
+__device__ __forceinline__ void fold_pair(ulonglong2* gb, ulonglong2* my_rows, uint32_t rs, uint32_t R, uint32_t d0,
+                                          uint64_t x0, uint64_t g0, uint32_t d1, uint64_t x1, uint64_t g1) {
+  if (max(d0, d1) < R) {
+    ulonglong2* p0 = my_rows + d0 * rs;
+    ulonglong2* p1 = my_rows + d1 * rs;
+    ulonglong2 v1 = *p1;
+    ulonglong2 v0 = *p0;
+    const uint64_t same = d0 == d1 ? ~0ull : 0ull;
+    v1.x ^= x1;
+    v1.y ^= g1;
+    v0.x ^= x0 ^ (x1 & same);
+    v0.y ^= g0 ^ (g1 & same);
+    *p1 = v1;
+    *p0 = v0;
+  } else {
+    fold_record(gb, my_rows, rs, R, d0, x0, g0);
+    fold_record(gb, my_rows, rs, R, d1, x1, g1);
+  }
+}
+
 // Fold the records rec[0..n) of one work item into the sketch of its vertex,
 // whose buckets for this lane start at gb. Records pass through shared
-// memory kStage at a time. Rows of a lane live at my_rows[d * rs]
+// memory one pass at a time; each thread loads its record of the next pass
+// while the current one folds. Rows of a lane live at my_rows[d * rs]
 // (rs = blockDim.x), so the lanes of a shared-memory phase hit distinct
 // 16-byte bank groups; a lane is the only writer of its rows, so no shared
 // atomics are needed. Four records at a time: their loads and depths are
-// independent, only the row read-modify-writes form a chain (two records
-// may share a row). `excl`: no other CTA writes this vertex, so the
-// write-back is a plain read-modify-write. Call from every thread.
+// independent, and they fold as two overlapping pairs. `excl`: no other CTA
+// writes this vertex, so the write-back is a plain read-modify-write. Call
+// from every thread.
 template <bool kLong>
 __device__ __forceinline__ void apply_item(const ApplyLane& l, ulonglong2* gb, const uint64_t* __restrict__ rec,
                                            uint32_t n, bool excl, uint32_t L, uint32_t R, const ApplySmem& m,
                                            ulonglong2* my_rows, uint32_t rs) {
-  if (l.active) {  // bring this lane's buckets to L2 for the write-back
-    prefetch_l2(gb);
-    if (l.nrows > 1) {
-      prefetch_l2(gb + 6);
-      prefetch_l2(gb + l.nrows - 1);
-    }
-  }
+  const uint32_t cs = stage_size(), tid = threadIdx.x;
   const uint64_t* gcol = m.g + l.layer;
-  const ulonglong2* x2 = reinterpret_cast<const ulonglong2*>(m.x);
-  for (uint32_t c0 = 0; c0 < n; c0 += kStage) {
-    const uint32_t nc = min(kStage, n - c0);
-    if (c0) __syncthreads();  // every lane is done with the previous pass
-    stage_records(l, m, rec + c0, nullptr, nc, L);
+  uint64_t xr = tid < n ? __ldg(rec + tid) : 0ull;
+  uint32_t buf = 0;
+  for (uint32_t c0 = 0; c0 < n; c0 += cs, buf ^= 1) {
+    const uint32_t nc = min(cs, n - c0);
+    const uint64_t* xs = stage_pass(l, m, xr, 0u, false, nc, L, buf);
+    const ulonglong2* x2 = reinterpret_cast<const ulonglong2*>(xs);
+    if (c0 + cs + tid < n) xr = __ldg(rec + c0 + cs + tid);  // the next pass, in flight during this one
     uint32_t i = 0;
     for (; i + 4 <= nc; i += 4) {
       const ulonglong2 xa = x2[i >> 1], xb = x2[(i >> 1) + 1];
@@ -305,11 +332,11 @@ __device__ __forceinline__ void apply_item(const ApplyLane& l, ulonglong2* gb, c
       for (int k = 0; k < 4; k++) gm[k] = gcol[(i + k) * L];
 #pragma unroll
       for (int k = 0; k < 4; k++) d[k] = lane_depth<kLong>(l, x[k]);
-#pragma unroll
-      for (int k = 0; k < 4; k++) fold_record(gb, my_rows, rs, R, d[k], x[k], gm[k]);
+      fold_pair(gb, my_rows, rs, R, d[0], x[0], gm[0], d[1], x[1], gm[1]);
+      fold_pair(gb, my_rows, rs, R, d[2], x[2], gm[2], d[3], x[3], gm[3]);
     }
     for (; i < nc; i++) {
-      const uint64_t x = m.x[i];
+      const uint64_t x = xs[i];
       fold_record(gb, my_rows, rs, R, lane_depth<kLong>(l, x), x, gcol[i * L]);
     }
   }
@@ -360,19 +387,23 @@ __device__ __forceinline__ void apply_direct(const ApplyLane& l, ulonglong2* ske
                                              uint32_t n, uint32_t L, const ApplySmem& m) {
   ulonglong2* lbase = sketch + (size_t)l.layer * V * W + l.jbase;
   const uint64_t* gcol = m.g + l.layer;
-  for (uint32_t c0 = 0; c0 < n; c0 += kStage) {
-    const uint32_t nc = min(kStage, n - c0);
-    if (c0) __syncthreads();
-    stage_records(l, m, rec + c0, recw + c0, nc, L);
+  const uint32_t cs = stage_size(), tid = threadIdx.x;
+  uint32_t buf = 0;
+  for (uint32_t c0 = 0; c0 < n; c0 += cs, buf ^= 1) {
+    const uint32_t nc = min(cs, n - c0);
+    const bool mine = tid < nc;
+    const uint64_t* xs =
+        stage_pass(l, m, mine ? __ldg(rec + c0 + tid) : 0ull, mine ? __ldg(recw + c0 + tid) : 0u, true, nc, L, buf);
+    const uint32_t* ws = m.w + buf * kStage;
     for (uint32_t i0 = 0; i0 < nc; i0 += 4) {
       uint64_t x[4], gm[4];
       uint32_t d[4], w[4];
 #pragma unroll
       for (uint32_t k = 0; k < 4; k++) {
         const uint32_t i = min(i0 + k, nc - 1);
-        x[k] = m.x[i];
+        x[k] = xs[i];
         gm[k] = gcol[i * L];
-        w[k] = m.w[i];
+        w[k] = ws[i];
       }
 #pragma unroll
       for (uint32_t k = 0; k < 4; k++) d[k] = lane_depth<kLong>(l, x[k]);

@@ -400,3 +400,41 @@ def round_robin(streams):
                 idx[i] += 1
                 live = True
     return order
+
+
+# ---- adversarial components: disjoint cliques joined and split by bridges ----
+
+def clique_stream(V: int = 131072, k: int = 256, s: int = 512, n_batches: int = 8, batch: int = 65536,
+                  seed: int = 7):
+    """k disjoint s-cliques on seeded permuted vertex ids, joined by
+    n_batches batches of `batch` distinct random bridge inserts between
+    different cliques, then split again by n_batches shuffled batches
+    deleting them; one 1k-pair Connected batch (500 pairs inside one clique,
+    500 across two) is asked after every bridge batch.
+
+    Returns (clique_edges [k*s*(s-1)/2, 2] uint32 in clique order,
+    bridge batches [(edges [batch, 2] uint32, op +1/-1)], pairs [1000, 2]
+    uint32, clique of every vertex [V] int64)."""
+    g = rng(seed)
+    perm = g.permutation(V).astype(np.uint32)
+    iu, ju = np.triu_indices(s, 1)
+    cl = np.concatenate([np.stack([perm[c * s + iu], perm[c * s + ju]], 1) for c in range(k)])
+    comp = np.empty(V, np.int64)
+    comp[perm] = np.repeat(np.arange(k), s)
+    nb = n_batches * batch
+    a = g.integers(0, V, 3 * nb)
+    b = g.integers(0, V, 3 * nb)
+    ok = comp[a] != comp[b]
+    bid = np.unique(np.minimum(a, b)[ok] * V + np.maximum(a, b)[ok])
+    bid = g.permutation(bid)[:nb]
+    bridges = np.stack([bid // V, bid % V], 1).astype(np.uint32)
+    dels = g.permutation(nb)
+    order = [(bridges[i * batch:(i + 1) * batch], 1) for i in range(n_batches)]
+    order += [(bridges[dels[i * batch:(i + 1) * batch]], -1) for i in range(n_batches)]
+    cs = g.integers(0, k, 500)
+    same = np.stack([perm[cs * s + g.integers(0, s, 500)], perm[cs * s + g.integers(0, s, 500)]], 1)
+    c1 = g.integers(0, k, 500)
+    c2 = (c1 + g.integers(1, k, 500)) % k
+    diff = np.stack([perm[c1 * s + g.integers(0, s, 500)], perm[c2 * s + g.integers(0, s, 500)]], 1)
+    pairs = np.ascontiguousarray(np.concatenate([same, diff])[g.permutation(1000)], np.uint32)
+    return cl, order, pairs, comp

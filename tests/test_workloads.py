@@ -110,3 +110,30 @@ def test_serving_streams_are_valid_per_graph():
         mine = [st for j, st in order if j == i]
         assert len(mine) == len(s[2]) and all(a is b for a, b in zip(mine, s[2]))
     assert [j for j, _ in order[:len(streams)]] == list(range(len(streams)))
+
+
+def test_clique_stream_is_a_valid_stream_of_the_stated_shape():
+    # small instance of the adversarial workload: cliques are complete and
+    # disjoint, bridges join different cliques, are distinct and absent from
+    # the cliques, every insert batch is deleted again in the second half
+    V, k, s = 64 * 8, 8, 64
+    cl, order, pairs, comp = WL.clique_stream(V=V, k=k, s=s, n_batches=2, batch=100, seed=3)
+    assert len(cl) == k * s * (s - 1) // 2
+    assert np.all(comp[cl[:, 0]] == comp[cl[:, 1]])
+    assert np.bincount(comp, minlength=k).tolist() == [s] * k
+    ids = np.minimum(cl[:, 0], cl[:, 1]).astype(np.int64) * V + np.maximum(cl[:, 0], cl[:, 1])
+    assert len(np.unique(ids)) == len(ids)
+    ins = np.concatenate([E for E, op in order if op == 1])
+    dels = np.concatenate([E for E, op in order if op == -1])
+    assert [op for _, op in order] == [1, 1, -1, -1]
+    assert np.all(comp[ins[:, 0]] != comp[ins[:, 1]])
+    bid = ins[:, 0].astype(np.int64) * V + ins[:, 1]
+    assert len(np.unique(bid)) == len(bid) == 200
+    assert np.all(ins[:, 0] < ins[:, 1])
+    assert np.array_equal(np.sort(bid), np.sort(dels[:, 0].astype(np.int64) * V + dels[:, 1]))
+    assert pairs.shape == (1000, 2)
+    same = comp[pairs[:, 0]] == comp[pairs[:, 1]]
+    assert same.sum() >= 500  # 500 drawn inside one clique (+ chance collisions of the rest: none, c1 != c2)
+    assert same.sum() == 500
+    a, b, c, d = WL.clique_stream(V=V, k=k, s=s, n_batches=2, batch=100, seed=3)
+    assert np.array_equal(a, cl) and np.array_equal(c, pairs)
