@@ -299,6 +299,50 @@ cupc_status cupc_build_info(int* binary_version, int* ptx_version);
  * CUDA context stays usable either way. */
 cupc_status cupc_selftest_wait_timeout(uint32_t ctas, uint32_t limit_us, int absent_cta, cupc_stream stream);
 
+/* ---- Parallel cutset (§3.1, Lemma 3.1): tree sketches of a dynamic forest.
+ *
+ * A cupc_cutset keeps, for a forest F of link/cut operations over the
+ * vertices of graph g, the sketch of every tree of F: the XOR of its
+ * vertices' sketches in g (all L layers), i.e. the sketch of the tree's cut
+ * (App. A.1.1: internal edges cancel). The forest is held as Euler tours in
+ * search trees on the host; every tree node has an aggregate sketch in
+ * device memory. A link or cut changes O(log V) aggregates; the sketch
+ * additions it needs are logged and the batch's log is replayed in one
+ * launch with one GPU thread per sketch word, each following the whole log
+ * for its word (§3.1's parallel execution of the logged additions).
+ *
+ * The cutset reads g's vertex sketches: after changing them (any update of
+ * g), REFRESH every vertex whose sketch changed. g must outlive the cutset.
+ * Device memory: 3*V aggregate sketches (3*V*L*W*16 bytes) plus the log. Not
+ * thread-safe; calls are ordered on `stream` and return after the replay
+ * has been enqueued and its log copied (they synchronise `stream`). */
+typedef struct cupc_cutset cupc_cutset;
+enum { CUPC_CUTSET_LINK = 1, CUPC_CUTSET_CUT = 2, CUPC_CUTSET_REFRESH = 3 };
+/* A cutset over g whose forest has no edge (every vertex its own tree). */
+cupc_status cupc_cutset_create(cupc_graph* g, cupc_stream stream, cupc_cutset** out);
+/* Apply n operations in order; ops (host) holds n triples {kind, u, v}:
+ * LINK adds forest edge (u,v) (u and v must be in different trees), CUT
+ * removes forest edge (u,v) (it must be in F), REFRESH (v ignored) recomputes
+ * the aggregates over vertex u after its sketch in g changed. The first
+ * invalid operation stops the batch: *applied (nullable) = the operations
+ * applied before it, whose additions are replayed, and CUPC_EINVAL is
+ * returned. */
+cupc_status cupc_cutset_apply(cupc_cutset* c, const uint32_t* ops, size_t n, size_t* applied, cupc_stream stream);
+/* *out = 1 if u and v are in one tree of F. Host only. */
+cupc_status cupc_cutset_connected(const cupc_cutset* c, uint32_t u, uint32_t v, int* out);
+/* The sketch of w's tree: L*W*16 bytes written to dst (device or host), laid
+ * out [layer][bucket]{alpha, gamma} as one vertex of cupc_export_sketches. */
+cupc_status cupc_cutset_tree_sketch(const cupc_cutset* c, uint32_t w, void* dst, cupc_stream stream);
+/* Query of the cutset (Lemma 3.1; §2.1): sample layer r of w's tree sketch:
+ * *result = 0 ZERO (no edge leaves the tree), 1 GOOD (*edge = u*V+v of an
+ * edge with one endpoint in the tree, w.h.p.), 2 FAIL; same rule as the
+ * recovery's sample. Synchronises `stream`. */
+cupc_status cupc_cutset_query(const cupc_cutset* c, uint32_t w, uint32_t r, uint32_t* result, uint64_t* edge,
+                              cupc_stream stream);
+/* out4 = {sketch additions replayed, replay launches, links, cuts}. */
+cupc_status cupc_cutset_stats(const cupc_cutset* c, uint64_t* out4);
+void cupc_cutset_destroy(cupc_cutset* c);
+
 /* ---- Update without any device allocation (the paper has no counterpart).
  *
  * For callers that cannot call cudaMalloc at all: code whose device memory

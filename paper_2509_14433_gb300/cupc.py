@@ -67,6 +67,13 @@ _SIGS = {
     "cupc_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "cupc_selftest_wait_timeout": (ctypes.c_int, [_u32, _u32, ctypes.c_int, _P]),
     "cupc_build_info": (ctypes.c_int, [_P, _P]),
+    "cupc_cutset_create": (ctypes.c_int, [_P, _P, _P]),
+    "cupc_cutset_apply": (ctypes.c_int, [_P, _P, _sz, _P, _P]),
+    "cupc_cutset_connected": (ctypes.c_int, [_P, _u32, _u32, _P]),
+    "cupc_cutset_tree_sketch": (ctypes.c_int, [_P, _u32, _P, _P]),
+    "cupc_cutset_query": (ctypes.c_int, [_P, _u32, _u32, _P, _P, _P]),
+    "cupc_cutset_stats": (ctypes.c_int, [_P, _P]),
+    "cupc_cutset_destroy": (None, [_P]),
     "cupc_update_sketch_static": (ctypes.c_int, [_P, _u32, _u64, _P, _P, _sz, _P, _P]),
 }
 for _name, (_res, _args) in _SIGS.items():
@@ -279,6 +286,48 @@ def cupc_destroy(g) -> None:
 
 def cupc_selftest_wait_timeout(ctas: int, limit_us: int, absent_cta: int, stream=None) -> int:
     return _lib.cupc_selftest_wait_timeout(ctas, limit_us, absent_cta, stream_handle(stream))
+
+
+CUPC_CUTSET_LINK, CUPC_CUTSET_CUT, CUPC_CUTSET_REFRESH = 1, 2, 3
+
+
+def cupc_cutset_create(g, stream=None):
+    """Returns (status, handle)."""
+    h = ctypes.c_void_p(0)
+    st = _lib.cupc_cutset_create(g, stream_handle(stream), ctypes.byref(h))
+    return st, h.value
+
+
+def cupc_cutset_apply(c, ops, stream=None):
+    """ops: host uint32 array of {kind, u, v} triples. Returns (status, applied)."""
+    n = ctypes.c_size_t(0)
+    st = _lib.cupc_cutset_apply(c, ptr(ops), len(ops) // 3, ctypes.byref(n), stream_handle(stream))
+    return st, n.value
+
+
+def cupc_cutset_connected(c, u: int, v: int):
+    out = ctypes.c_int(0)
+    st = _lib.cupc_cutset_connected(c, u, v, ctypes.byref(out))
+    return st, bool(out.value)
+
+
+def cupc_cutset_tree_sketch(c, w: int, dst, stream=None) -> int:
+    return _lib.cupc_cutset_tree_sketch(c, w, ptr(dst), stream_handle(stream))
+
+
+def cupc_cutset_query(c, w: int, r: int, stream=None):
+    """Returns (status, result 0/1/2, edge)."""
+    res, e = ctypes.c_uint32(0), ctypes.c_uint64(0)
+    st = _lib.cupc_cutset_query(c, w, r, ctypes.byref(res), ctypes.byref(e), stream_handle(stream))
+    return st, res.value, e.value
+
+
+def cupc_cutset_stats(c, out4) -> int:
+    return _lib.cupc_cutset_stats(c, ptr(out4))
+
+
+def cupc_cutset_destroy(c) -> None:
+    _lib.cupc_cutset_destroy(c)
 
 
 def cupc_build_info():
