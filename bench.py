@@ -1032,6 +1032,105 @@ def paper_stream(torch, C, dev, stream):
     return res
 
 
+PAPER_TABLE1 = {  # CUPCaKE on a 48-core EPYC 7643 (context only): updates/s, queries/s
+    13: {"standard": (1.79e6, 3.37e6), "fixed_forest": (4.56e6, 6.92e6)},
+    15: {"standard": (0.84e6, 1.72e6), "fixed_forest": (2.19e6, 3.75e6)},
+    16: {"standard": (0.88e6, 1.87e6), "fixed_forest": (1.75e6, 2.99e6)},
+    17: {"standard": (0.61e6, 1.35e6), "fixed_forest": (1.63e6, 2.81e6)},
+}
+
+
+def run_paper_streams(args):
+    """The paper's stream shapes (§5 datasets, App. C) on Kronecker-shaped
+    graphs of V = 2^levels at density 0.5 (workloads.kronecker_graph): the
+    standard stream (insert every edge, then delete every edge, each phase in
+    a fresh random order) and the fixed forest stream (insert a spanning
+    forest, then insert every other edge and delete it again), with a burst
+    of rho/9 uniform Connected pairs after every rho ~ U[1000, 2000]
+    updates. Each whole stream runs once with incremental labels (and, for
+    the smallest graph, once with a full recovery per burst): updates/s and
+    queries/s over the whole stream, the recoveries it ran. Prints one JSON
+    line per (graph, stream, mode)."""
+    import torch
+
+    from paper_2509_14433_gb300 import cupc as C
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    for levels in [int(x) for x in args.kron.split(",")]:
+        V = 1 << levels
+        gen = torch.Generator(device=dev).manual_seed(100 + levels)
+        t0 = time.perf_counter()
+        ids, parent = WL.kronecker_graph(levels, 100 + levels, device=dev)
+        t_gen = time.perf_counter() - t0
+        m = ids.numel()
+        ar = torch.arange(V, device=dev)
+        fmask = parent != ar
+        forest = parent[fmask] * V + ar[fmask]
+        roots = int((~fmask).sum())
+        st, g = C.cupc_init(V, SEED, (0, 0, 0, 1 << 16), None, stream)
+        C.check(st)
+        stats = np.zeros(8, np.uint64)
+        for shape in ("standard", "fixed_forest"):
+            if shape == "standard":
+                seq = torch.cat([ids[torch.randperm(m, generator=gen, device=dev)],
+                                 ids[torch.randperm(m, generator=gen, device=dev)]])
+                ops = torch.cat([torch.ones(m, dtype=torch.int8, device=dev),
+                                 -torch.ones(m, dtype=torch.int8, device=dev)])
+            else:
+                rest = ids[~torch.isin(ids, forest)]
+                k = rest.numel()
+                seq = torch.cat([forest, rest[torch.randperm(k, generator=gen, device=dev)],
+                                 rest[torch.randperm(k, generator=gen, device=dev)]])
+                ops = torch.cat([torch.ones(forest.numel() + k, dtype=torch.int8, device=dev),
+                                 -torch.ones(k, dtype=torch.int8, device=dev)])
+                del rest
+            n = seq.numel()
+            E = torch.stack([seq // V, seq % V], 1).to(torch.int32).contiguous()
+            del seq
+            rng = WL.rng(17 + levels)
+            rho = rng.integers(1000, 2001, size=n // 1000 + 2)
+            starts = np.concatenate([[0], np.cumsum(rho)])
+            nb = int(np.searchsorted(starts, n))
+            starts = np.minimum(starts[:nb + 1], n)
+            qn = np.maximum(1, (starts[1:] - starts[:-1]) // 9)
+            qoff = np.concatenate([[0], np.cumsum(qn)])
+            P = torch.randint(0, V, (2 * int(qoff[-1]),), generator=gen, device=dev, dtype=torch.int32)
+            out = torch.empty(int(qoff[-1]), dtype=torch.uint8, device=dev)
+            e_ptr, o_ptr, p_ptr, a_ptr = E.data_ptr(), ops.data_ptr(), P.data_ptr(), out.data_ptr()
+            modes = (("incremental_labels", 1),) + ((("recovery_per_burst", 0),) if levels <= 13 else ())
+            for mode, inc in modes:
+                C.check(C.cupc_set_incremental(g, inc, stream))
+                C.check(C.cupc_reset(g, stream))
+                C.check(C.cupc_stats(g, stats, stream))
+                r0 = int(stats[5])
+                torch.cuda.synchronize()
+                t = time.perf_counter()
+                for b in range(nb):
+                    a, z = int(starts[b]), int(starts[b + 1])
+                    C.check(C.cupc_update_batch(g, e_ptr + 8 * a, o_ptr + a, z - a, stream))
+                    q0, q1 = int(qoff[b]), int(qoff[b + 1])
+                    C.check(C.cupc_query(g, p_ptr + 8 * q0, q1 - q0, a_ptr + q0, stream), "query",
+                            ok=(C.CUPC_OK, C.CUPC_EINCOMPLETE))
+                torch.cuda.synchronize()
+                dt = time.perf_counter() - t
+                C.check(C.cupc_stats(g, stats, stream))
+                pu, pq = PAPER_TABLE1[levels][shape]
+                print(json.dumps({"graph": f"Kronecker V=2^{levels} density 0.5", "edges": m, "forest_roots": roots,
+                                  "stream": shape, "mode": mode, "updates": n, "queries": int(qoff[-1]),
+                                  "bursts": nb, "seconds": dt, "updates_per_s": n / dt,
+                                  "queries_per_s": int(qoff[-1]) / dt, "recoveries": int(stats[5]) - r0,
+                                  "generation_s": t_gen,
+                                  "paper_cupcake_48core_epyc": {"updates_per_s": pu, "queries_per_s": pq}}),
+                      flush=True)
+            del E, ops, P, out
+            torch.cuda.empty_cache()
+        C.check(C.cupc_sync(g, stream), "paper streams", ok=(C.CUPC_OK, C.CUPC_EINCOMPLETE))
+        C.cupc_destroy(g)
+        del ids, parent, forest
+        torch.cuda.empty_cache()
+
+
 def run_apply_profile(args):
     """Small cases for ncu. dense: a V=16384 graph (826 MB of sketches,
     larger than L2) receives the first 8 insert batches of the dense stream.
@@ -1074,7 +1173,8 @@ def run_apply_profile(args):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--mode", default="bench", choices=["bench", "apply-profile"])
+    ap.add_argument("--mode", default="bench", choices=["bench", "apply-profile", "paper-streams"])
+    ap.add_argument("--kron", default="13,15,16", help="paper-streams: Kronecker graph sizes (log2 V)")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
@@ -1086,6 +1186,8 @@ def main():
     args = ap.parse_args()
     if args.mode == "apply-profile":
         run_apply_profile(args)
+    elif args.mode == "paper-streams":
+        run_paper_streams(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

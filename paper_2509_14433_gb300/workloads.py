@@ -438,3 +438,52 @@ def clique_stream(V: int = 131072, k: int = 256, s: int = 512, n_batches: int = 
     diff = np.stack([perm[c1 * s + g.integers(0, s, 500)], perm[c2 * s + g.integers(0, s, 500)]], 1)
     pairs = np.ascontiguousarray(np.concatenate([same, diff])[g.permutation(1000)], np.uint32)
     return cl, order, pairs, comp
+
+
+# ---- Kronecker-shaped dense graphs (the paper's K13..K17 shape) --------------
+
+def kronecker_b(levels: int, density: float = 0.5) -> float:
+    """Entry b of the rank-one initiator [[1, b], [b, b^2]] whose k-th
+    Kronecker power has mean entry ((1 + b) / 2)^(2k) = density."""
+    return 2.0 * density ** (1.0 / (2 * levels)) - 1.0
+
+
+def kronecker_graph(levels: int, seed: int, device="cpu", density: float = 0.5, block_pairs: int = 1 << 27):
+    """Stochastic Kronecker graph (Leskovec, Chakrabarti, Kleinberg,
+    Faloutsos, Ghahramani, JMLR 2010) on V = 2^levels vertices with the
+    initiator [[1, b], [b, b^2]] (b = kronecker_b(levels, density)): each
+    pair u < v is an edge independently with probability
+    b^(popcount(u) + popcount(v)), the product over the levels of the
+    initiator entry picked by the two vertices' bits. The expected density
+    is `density` (0.5: the density of the paper's Kronecker datasets), with
+    degrees skewed towards vertices of few one-bits.
+
+    Drawn on `device` (torch) in blocks of rows. Returns (edge ids u*V+v
+    int64 ascending, parent int64 [V]): parent[v] = the smallest neighbour
+    u < v of v, or v itself when it has none, so the edges (parent[v], v),
+    v != parent[v], form a spanning forest of every component whose
+    vertices other than its minimum have a smaller neighbour."""
+    import torch
+    V = 1 << levels
+    b = kronecker_b(levels, density)
+    dev = torch.device(device)
+    gen = torch.Generator(device=dev).manual_seed(seed)
+    pc = torch.zeros(V, dtype=torch.int64, device=dev)
+    ar = torch.arange(V, device=dev)
+    for lv in range(levels):
+        pc += (ar >> lv) & 1
+    w = torch.pow(torch.tensor(b, dtype=torch.float64, device=dev), pc.double()).float()
+    rows = max(1, min(V, block_pairs // V))
+    parts = []
+    parent = ar.clone()
+    for u0 in range(0, V, rows):
+        u1 = min(V, u0 + rows)
+        p = w[u0:u1, None] * w[None, :]
+        keep = torch.rand((u1 - u0, V), generator=gen, device=dev) < p
+        keep &= ar[None, :] > ar[u0:u1, None]
+        ru, v = torch.nonzero(keep, as_tuple=True)
+        u = ru + u0
+        parts.append(u * V + v)
+        parent.scatter_reduce_(0, v, u, "amin")
+        del p, keep
+    return torch.cat(parts), parent
