@@ -296,18 +296,24 @@ def run_reference(args):
     if rank != 0:
         return
     import torch
-    dev = "cuda" if torch.cuda.is_available() else "cpu"
-    # the headline stream's first batches (same generator and seed)
-    s = WL.RmatStream(levels=RMAT_LEVELS, seed=RMAT_SEED, device=dev)
-    parts, n, sizes = [], 0, []
-    while n < REF_RMAT_SAMPLE:
-        e, _ = s.next_batch()
-        parts.append(e.cpu().numpy().astype(np.uint32))
-        n += len(e)
-        sizes.append(len(e))
-    E_h = np.concatenate(parts)
-    del s
-    cfg = headline_config(RMAT_UPDATES, 0, [1000, MAXB])
+    if torch.cuda.is_available():
+        # the headline stream itself (the generator runs on the device; no
+        # library code is involved), for its first updates and its shape
+        E, O, offs, _ = gen_rmat_stream(torch, torch.device("cuda", 0))
+        E_h = E[:REF_RMAT_SAMPLE].cpu().numpy().astype(np.uint32)
+        cfg = headline_config(int(offs[-1]), len(offs) - 1, np.diff(offs).astype(np.int64))
+        del E, O
+        torch.cuda.empty_cache()
+    else:  # the same generator and seed on the host: its first batches
+        s = WL.RmatStream(levels=RMAT_LEVELS, seed=RMAT_SEED, device="cpu")
+        parts, n = [], 0
+        while n < REF_RMAT_SAMPLE:
+            e, _ = s.next_batch()
+            parts.append(e.numpy().astype(np.uint32))
+            n += len(e)
+        E_h = np.concatenate(parts)
+        del s
+        cfg = headline_config(RMAT_UPDATES, 0, [1000, MAXB])
     cfg["sample"] = (f"per step: the oracle on the first {REF_RMAT_SAMPLE} updates of this stream, one 1k-pair "
                      "Connected batch and the spanning forest (single thread)")
     for _ in range(args.warmup):
@@ -532,14 +538,13 @@ def run_gpu(args):
 
     if rank == 0:
         cfg = headline_config(n, nb, sizes)
-        cfg["apply_tuning_buckets_set"] = n_buckets
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
                 "config": cfg,
                 "e2e": {"value": e2e_val, "unit": UNIT,
                         "h2d_bytes_per_step": int(9 * n + 8000), "d2h_bytes_per_step": int(1000 + 8 * nf_h)},
-                "gpu_launches": gpu_launches,
+                "gpu_launches": gpu_launches, "apply_tuning_buckets_set": n_buckets,
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                              "frac": achieved / peak, "traffic": apply_traffic("rmat_v131072"),
                              "kernel": "k_apply", "algorithmic_bytes_per_launch": apply_bytes_per_launch,

@@ -140,7 +140,12 @@ struct cupc_server {
   // most one request in flight)
   uint32_t* stat_words = nullptr;
   std::vector<uint32_t> free_slots;
+  // updates run on one stream at the lowest priority, queries on streams at
+  // the highest: when a kernel ends, a waiting query's kernels start before
+  // the next update's, so a query waits at most for the update kernel running
+  // when it arrives
   cudaStream_t upd_stream = nullptr;
+  int prio_low = 0, prio_high = 0;
   std::vector<cudaStream_t> q_streams;
   std::vector<uint32_t*> q_pairs;  // device staging per query stream
   std::vector<uint8_t*> q_out;
@@ -231,8 +236,14 @@ void admit(cupc_server* s) {
   }
 }
 
+// Edges one multi-graph update launch joins at most, and how long the worker
+// keeps polling after its last activity before it sleeps.
+constexpr size_t kLaunchEdges = (size_t)1 << 18;
+constexpr int kIdleSpinUs = 500;
+
 void worker_loop(cupc_server* s) {
   cudaSetDevice(s->device);
+  Clock::time_point last_busy = Clock::now();
   std::unique_lock<std::mutex> lk(s->mu);
   while (true) {
     if (s->stop && s->inflight.empty()) break;
@@ -264,10 +275,13 @@ void worker_loop(cupc_server* s) {
     if (completed) s->cv_done.notify_all();
     (void)now;
 
-    // gather: next request of every idle resident graph
+    // gather: next request of every idle resident graph; one update launch
+    // joins at most kLaunchEdges edges over its graphs (a single larger
+    // request goes alone), which bounds how long a query can wait for it
     std::vector<uint64_t> upd_insts;
     std::vector<std::vector<Request>> upd_reqs;
     std::vector<size_t> upd_n;
+    size_t launch_edges = 0;
     for (auto& kv : s->inst) {
       Instance& in = kv.second;
       if (!in.resident || in.busy || in.q.empty()) continue;
@@ -326,14 +340,20 @@ void worker_loop(cupc_server* s) {
         s->stat[1] += r.n;
         continue;
       }
-      // join consecutive updates (up to max_batch edges)
+      // join consecutive updates (up to max_batch edges, and up to the
+      // launch's remaining budget unless this graph would be its first)
+      if (in.q.front().n <= s->cfg.max_batch && !upd_insts.empty() &&
+          launch_edges + in.q.front().n > kLaunchEdges)
+        continue;  // the next launch takes it
       std::vector<Request> joined;
       size_t n = 0;
-      while (!in.q.empty() && in.q.front().kind == K_UPDATE && n + in.q.front().n <= s->cfg.max_batch) {
+      while (!in.q.empty() && in.q.front().kind == K_UPDATE && n + in.q.front().n <= s->cfg.max_batch &&
+             (joined.empty() || launch_edges + n + in.q.front().n <= kLaunchEdges)) {
         n += in.q.front().n;
         joined.push_back(in.q.front());
         in.q.pop_front();
       }
+      launch_edges += n;
       if (joined.empty()) {  // a single request above max_batch: reject it
         Request r = in.q.front();
         in.q.pop_front();
@@ -366,8 +386,13 @@ void worker_loop(cupc_server* s) {
         s->stat[0] += upd_n[i];
         s->stat[3] += upd_reqs[i].size();
       }
-      cupc_batcher_update(s->batcher, gs.data(), es.data(), os.data(), upd_n.data(), (uint32_t)gs.size(),
-                          (cupc_stream)s->upd_stream);
+      // one graph: its own launch sequence (a plan over many CTAs); several:
+      // one multi-graph launch
+      if (gs.size() == 1)
+        cupc_update_batch(gs[0], es[0], os[0], upd_n[0], (cupc_stream)s->upd_stream);
+      else
+        cupc_batcher_update(s->batcher, gs.data(), es.data(), os.data(), upd_n.data(), (uint32_t)gs.size(),
+                            (cupc_stream)s->upd_stream);
       s->stat[2]++;
       Inflight f;
       f.kind = K_UPDATE;
@@ -385,8 +410,10 @@ void worker_loop(cupc_server* s) {
         }
       s->inflight.push_back(f);
     }
-    // wait for work or completions
-    if (s->inflight.empty()) {
+    // wait for work or completions: poll while busy and for a short while
+    // after (a request arriving then is picked up at once), then sleep
+    if (!s->inflight.empty() || !upd_insts.empty()) last_busy = Clock::now();
+    if (s->inflight.empty() && Clock::now() - last_busy > std::chrono::microseconds(kIdleSpinUs)) {
       s->cv_work.wait_for(lk, std::chrono::milliseconds(2));
     } else {
       lk.unlock();
@@ -403,7 +430,6 @@ uint64_t submit(cupc_server* s, uint64_t id, Request r, cupc_status* st) {
     return 0;
   }
   r.ticket = s->next_ticket++;
-  r.t_submit = Clock::now();
   s->tickets[r.ticket] = Ticket();
   it->second.q.push_back(r);
   *st = CUPC_OK;
@@ -427,13 +453,14 @@ cupc_status cupc_server_create(const cupc_server_config* cfg, cupc_server** out)
   bool ok = cudaGetDevice(&s->device) == cudaSuccess && cudaMalloc(&s->arena, cfg->mem_bytes) == cudaSuccess &&
             cudaMallocHost((void**)&s->pinned, s->cfg.pinned_bytes) == cudaSuccess &&
             cudaMallocHost((void**)&s->stat_words, 4 * (size_t)cfg->max_graphs) == cudaSuccess &&
-            cudaStreamCreateWithFlags(&s->upd_stream, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaDeviceGetStreamPriorityRange(&s->prio_low, &s->prio_high) == cudaSuccess &&
+            cudaStreamCreateWithPriority(&s->upd_stream, cudaStreamNonBlocking, s->prio_low) == cudaSuccess &&
             cupc_batcher_create(cfg->max_graphs, 1, &s->batcher) == CUPC_OK;
   for (uint32_t i = 0; ok && i < s->cfg.query_streams; i++) {
     cudaStream_t qs;
     uint32_t* qp = nullptr;
     uint8_t* qo = nullptr;
-    ok = cudaStreamCreateWithFlags(&qs, cudaStreamNonBlocking) == cudaSuccess &&
+    ok = cudaStreamCreateWithPriority(&qs, cudaStreamNonBlocking, s->prio_high) == cudaSuccess &&
          cudaMalloc((void**)&qp, (size_t)s->cfg.max_batch * 8) == cudaSuccess &&
          cudaMalloc((void**)&qo, s->cfg.max_batch) == cudaSuccess;
     if (ok) {
@@ -487,12 +514,16 @@ cupc_status cupc_server_update(cupc_server* s, uint64_t id, const uint32_t* edge
   r.kind = K_UPDATE;
   r.n = n;
   r.pin_bytes = n * 9;
-  std::lock_guard<std::mutex> lk(s->mu);
-  if (r.pin_bytes && !s->pin_alloc.alloc(r.pin_bytes, 16, &r.pin_off)) return CUPC_ENOMEM;
-  if (n) {
+  r.t_submit = Clock::now();  // latency counts from here, the payload copy included
+  if (r.pin_bytes) {
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (!s->pin_alloc.alloc(r.pin_bytes, 16, &r.pin_off)) return CUPC_ENOMEM;
+  }
+  if (n) {  // the range is this request's: copy without holding the server lock
     memcpy(s->pinned + r.pin_off, edges, n * 8);
     memcpy(s->pinned + r.pin_off + n * 8, ops, n);
   }
+  std::lock_guard<std::mutex> lk(s->mu);
   cupc_status st;
   *ticket = submit(s, id, r, &st);
   if (st != CUPC_OK && r.pin_bytes) s->pin_alloc.release(r.pin_off);
@@ -507,9 +538,13 @@ cupc_status cupc_server_query(cupc_server* s, uint64_t id, const uint32_t* pairs
   r.n = m;
   r.pin_bytes = m * 8;
   r.user_out = out;
-  std::lock_guard<std::mutex> lk(s->mu);
-  if (!s->pin_alloc.alloc(r.pin_bytes, 16, &r.pin_off)) return CUPC_ENOMEM;
+  r.t_submit = Clock::now();
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (!s->pin_alloc.alloc(r.pin_bytes, 16, &r.pin_off)) return CUPC_ENOMEM;
+  }
   memcpy(s->pinned + r.pin_off, pairs, m * 8);
+  std::lock_guard<std::mutex> lk(s->mu);
   cupc_status st;
   *ticket = submit(s, id, r, &st);
   if (st != CUPC_OK) s->pin_alloc.release(r.pin_off);
@@ -520,6 +555,7 @@ cupc_status cupc_server_close(cupc_server* s, uint64_t id, uint64_t* ticket) {
   if (!s || !ticket) return CUPC_EINVAL;
   Request r{};
   r.kind = K_CLOSE;
+  r.t_submit = Clock::now();
   std::lock_guard<std::mutex> lk(s->mu);
   cupc_status st;
   *ticket = submit(s, id, r, &st);
