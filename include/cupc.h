@@ -113,11 +113,12 @@ cupc_status cupc_update_batch(cupc_graph* g, const uint32_t* edges, const int8_t
  * edge of the kept spanning forest (the recovered forest plus these edges),
  * and a delete outside that forest changes nothing, so a query then skips
  * the Boruvka recovery. Deleting a kept forest edge makes the next query
- * recover from the fragments of the remaining forest (a warm start). A batch
- * that both merges components and deletes edges (its order inside the batch
- * is not followed), a reset, an import, a host batch staged in several
- * chunks or a cupc_batcher update clears the labels, and the next query
- * recovers in full. This relies on the stream
+ * recover from the fragments of the remaining forest (a warm start); a
+ * batch may both merge components and delete edges, in any valid order
+ * (an edge it inserts and then deletes again is found in the kept forest).
+ * A reset, an import, a host batch staged in several chunks or a
+ * cupc_batcher update clears the labels, and the next query recovers in
+ * full. This relies on the stream
  * being valid (insert only absent edges, delete only present ones); with an
  * invalid stream the sketches toggle while the labels merge, and answers can
  * differ from a recovery's. cupc_spanning_forest always returns the forest

@@ -391,9 +391,6 @@ __global__ void __launch_bounds__(kRecThreads, 2) k_recover(RecArgs a) {
   if (a.inc)  // the merge-edge table starts empty (fadd itself is read by a warm start below)
     for (size_t i = gtid; i < ((size_t)1 << a.ftab_bits); i += gstride) a.ftab[i] = 0ull;
   if (gtid == 0) {
-    gc[GC_LABELS_VALID] = 0;
-    gc[GC_FOREST_SORTED] = 0;
-    gc[GC_WARM] = 0;
     gc[GC_NLIVE] = 0;
     gc[GC_NFOREST] = 0;
     gc[GC_NFAIL] = 0;
@@ -413,9 +410,12 @@ __global__ void __launch_bounds__(kRecThreads, 2) k_recover(RecArgs a) {
     a.log_ncand[r] = 0;
   }
   CUPC_GRID_SYNC();
-  if (gtid == 0) {  // every CTA has read them
+  if (gtid == 0) {  // every CTA has read them (the early return and warm above depend on them)
     if (dirty) gc[GC_REC_DIRTY] = 0;
     gc[GC_NFADD] = 0;
+    gc[GC_LABELS_VALID] = 0;
+    gc[GC_FOREST_SORTED] = 0;
+    gc[GC_WARM] = 0;
   }
   if (warm) {
     // fragments: union the endpoints of the forest edges still present (the

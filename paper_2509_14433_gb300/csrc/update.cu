@@ -152,9 +152,9 @@ __global__ void __launch_bounds__(1024) k_scatter_priv(const uint32_t* __restric
 // the recovered forest plus these edges stays a spanning forest of the
 // graph. A deleted forest edge of either kind is marked (fdead, fadd_dead)
 // and sets GC_WARM: the next recovery starts from the fragments of the
-// remaining forest. A batch that both merges and deletes clears
-// GC_LABELS_VALID (its order inside the batch is not followed) and the next
-// query recovers in full.
+// remaining forest. In a batch that both merges and deletes, an edge the
+// batch inserts (a merge) and then deletes is found by a second lookup pass
+// (k_incr_dead) once all of the batch's merges are recorded.
 __device__ __forceinline__ uint32_t inc_find(uint32_t* par, uint32_t x, uint32_t V) {
   for (uint32_t k = 0; k < V; k++) {  // a path is shorter than V
     const uint32_t y = ld_cg(&par[x]);
@@ -261,14 +261,43 @@ __global__ void k_incr(const uint32_t* __restrict__ edges, const int8_t* __restr
   if (__any_sync(0xffffffffu, warm) && (threadIdx.x & 31) == 0) gc[GC_WARM] = 1;
 }
 
-// Labels after the merges: every vertex takes its label's root. A batch
-// that merged and deleted clears the labels instead.
+// A batch that both merges and deletes: k_incr looked each delete up in the
+// merge edges recorded before the batch, so an edge this batch inserted (and
+// recorded as a merge) and then deleted again, in stream order, is looked up
+// again here, once every merge of the batch is in the table.
+__global__ void k_incr_dead(const uint32_t* __restrict__ edges, const int8_t* __restrict__ ops, size_t n,
+                            IncArgs a) {
+  uint32_t* gc = a.gc;
+  if ((ld_cg(&gc[GC_ERR]) & kErrInval) || !ld_cg(&gc[GC_LABELS_VALID]) || !ld_cg(&gc[GC_BATCH_MERGE]) ||
+      !ld_cg(&gc[GC_BATCH_DEL]))
+    return;
+  const uint32_t V = a.V, mask = (1u << a.ftab_bits) - 1u;
+  bool warm = false;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    if (ops[i] >= 0) continue;
+    const uint32_t u = edges[2 * i], v = edges[2 * i + 1];
+    const uint64_t id = (uint64_t)min(u, v) * V + max(u, v);
+    uint32_t sl = ftab_home(id, a.ftab_bits);
+    for (uint32_t k = 0; k <= mask; k++, sl = (sl + 1) & mask) {
+      const unsigned long long key = ld_cg((const uint64_t*)&a.ftab[sl]);
+      if (key == 0ull) break;
+      if (key == (unsigned long long)id) {
+        const uint32_t j = ld_cg(&a.ftab_pos[sl]);
+        if (j < V) a.fadd_dead[j] = 1;
+        warm = true;
+        break;
+      }
+    }
+  }
+  if (__any_sync(0xffffffffu, warm) && (threadIdx.x & 31) == 0) gc[GC_WARM] = 1;
+}
+
+// Labels after the merges: every vertex takes its label's root. Merges are
+// exact whatever else the batch did: a delete can only split components,
+// and one that removed a forest edge has set GC_WARM, so the next query
+// recovers from the fragments of the remaining forest.
 __global__ void k_incr_finish(uint32_t* label, uint32_t* ipar, uint32_t V, uint32_t* gc) {
   if (!ld_cg(&gc[GC_LABELS_VALID]) || !ld_cg(&gc[GC_BATCH_MERGE])) return;
-  if (ld_cg(&gc[GC_BATCH_DEL])) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) gc[GC_LABELS_VALID] = 0;
-    return;
-  }
   for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < V; w += gridDim.x * blockDim.x)
     label[w] = inc_find(ipar, label[w], V);
 }
@@ -292,6 +321,7 @@ cudaError_t launch_incremental(cupc_graph* g, const uint32_t* edges, const int8_
   a.gc = g->gc;
   const int grid = (int)std::min<size_t>((n + 255) / 256, (size_t)g->sms * 8);
   k_incr<<<grid, 256, 0, s>>>(edges, ops, n, a);
+  k_incr_dead<<<grid, 256, 0, s>>>(edges, ops, n, a);
   k_incr_finish<<<(int)std::min<size_t>((g->V + 255) / 256, (size_t)g->sms * 4), 256, 0, s>>>(g->label, g->ipar,
                                                                                                 g->V, g->gc);
   return cudaGetLastError();

@@ -217,3 +217,56 @@ def test_batcher_updates_drop_incremental_labels():
         assert np.array_equal(dev.labels(), ref.labels())
     finally:
         C.cupc_batcher_destroy(b)
+
+
+def test_mixed_batches_keep_the_labels_and_follow_the_order_inside_a_batch():
+    # batches that both merge components and delete edges, in a valid order
+    # inside the batch: deletes of present edges (forest edges among them),
+    # inserts that merge, and inserts deleted again later in the same batch
+    # (an edge that joined two components and is removed at once). Every
+    # answer equals the oracle's full recovery; batches whose deletes miss
+    # the kept forest need no recovery.
+    from paper_2509_14433_gb300 import cupc as C
+    V, seed = 800, 12
+    g = WL.rng(seed)
+    dev, ref = _dev(V, seed), O.Graph(V, seed)
+    assert C.cupc_set_incremental(dev.h, 1, None) == 0
+    E0 = WL.er_edges(V, 0.0015, seed)
+    present = set(int(a) * V + int(b) for a, b in E0)
+    assert dev.update(E0) == 0 and ref.update(E0) == O.OK
+    pairs = WL.uniform_pairs(V, 600, g, distinct=False)
+    assert np.array_equal(dev.query(pairs)[1], ref.query(pairs)[1])
+    rec0 = dev.stats()["recoveries"]
+    for step in range(30):
+        ids = np.array(sorted(present), np.int64)
+        pick = ids[g.choice(len(ids), int(g.integers(1, 25)), replace=False)]
+        D = np.stack([pick // V, pick % V], 1).astype(np.uint32)
+        present.difference_update(int(x) for x in pick)
+        I = _absent_pairs(V, int(g.integers(5, 80)), present, g)
+        again = I[: int(g.integers(0, 4))]  # inserted, then deleted again in this batch
+        present.update(int(a) * V + int(b) for a, b in I[len(again):])
+        E = np.concatenate([D, I, again])
+        ops = np.concatenate([-np.ones(len(D), np.int8), np.ones(len(I), np.int8), -np.ones(len(again), np.int8)])
+        assert dev.update(E, ops) == 0 and ref.update(E, ops) == O.OK
+        pairs = WL.uniform_pairs(V, 600, g, distinct=False)
+        s1, a1 = dev.query(pairs)
+        s2, a2 = ref.query(pairs)
+        assert s1 == s2 == 0 and np.array_equal(a1, a2), step
+        assert np.array_equal(dev.labels(), ref.labels()), step
+    # at most one recovery per query (a warm one after a forest edge went)
+    assert dev.stats()["recoveries"] - rec0 <= 30
+    ids = np.array(sorted(present), np.int64)
+    # a batch that merges and deletes only edges outside the kept forest:
+    # no recovery at all
+    st, forest = dev.forest()
+    fset = set(int(x) for x in forest)
+    nonf = np.array([x for x in ids.tolist() if x not in fset][:10], np.int64)
+    rec1 = dev.stats()["recoveries"]
+    I = _absent_pairs(V, 40, present, g)
+    E = np.concatenate([np.stack([nonf // V, nonf % V], 1).astype(np.uint32), I])
+    ops = np.concatenate([-np.ones(len(nonf), np.int8), np.ones(len(I), np.int8)])
+    assert dev.update(E, ops) == 0 and ref.update(E, ops) == O.OK
+    pairs = WL.uniform_pairs(V, 600, g, distinct=False)
+    assert np.array_equal(dev.query(pairs)[1], ref.query(pairs)[1])
+    assert dev.stats()["recoveries"] == rec1
+
