@@ -137,3 +137,31 @@ def test_clique_stream_is_a_valid_stream_of_the_stated_shape():
     assert same.sum() == 500
     a, b, c, d = WL.clique_stream(V=V, k=k, s=s, n_batches=2, batch=100, seed=3)
     assert np.array_equal(a, cl) and np.array_equal(c, pairs)
+
+
+def test_kronecker_graph_density_skew_and_forest():
+    # the initiator [[1, b], [b, b^2]] at density 0.5: mean entry
+    # ((1 + b) / 2)^(2k) = 0.5; pair (u, v) is an edge with probability
+    # b^(popcount u + popcount v); parent[v] is v's smallest neighbour
+    import torch
+    k = 9
+    b = WL.kronecker_b(k)
+    assert abs(((1 + b) / 2) ** (2 * k) - 0.5) < 1e-12
+    V = 1 << k
+    ids, parent = WL.kronecker_graph(k, 3)
+    ids = ids.numpy()
+    parent = parent.numpy()
+    n_pairs = V * (V - 1) // 2
+    p = np.array([[b ** (bin(u).count("1") + bin(v).count("1")) for v in range(V)] for u in range(V)])
+    want = p[np.triu_indices(V, 1)].sum()
+    sd = np.sqrt((p[np.triu_indices(V, 1)] * (1 - p[np.triu_indices(V, 1)])).sum())
+    assert abs(len(ids) - want) < 5 * sd and abs(len(ids) / n_pairs - 0.5) < 0.02
+    u, v = ids // V, ids % V
+    assert np.all(u < v) and np.all(np.diff(ids) != 0)
+    deg = np.bincount(np.concatenate([u, v]), minlength=V)
+    assert deg[0] > deg[V - 1]  # fewer one-bits: more neighbours
+    # parent: the smallest neighbour below v, else v itself
+    for w in (1, 5, V // 2, V - 1):
+        nb = np.concatenate([u[v == w]])
+        assert parent[w] == (nb.min() if nb.size else w)
+    assert torch.equal(WL.kronecker_graph(k, 3)[0], torch.from_numpy(ids))
