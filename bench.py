@@ -1045,6 +1045,27 @@ PAPER_TABLE1 = {  # CUPCaKE on a 48-core EPYC 7643 (context only): updates/s, qu
 }
 
 
+PERM_ONE = (1 << 31) - 1  # torch's device sorts (randperm) take at most this many elements
+PERM_CHUNK = 1 << 30
+
+
+def shuffled_parts(x, gen):
+    """The elements of x in a random order, as a sequence of tensors. Up to
+    PERM_ONE elements: one uniform permutation. Above: x is dealt into
+    c = ceil(len / PERM_CHUNK) strided subsequences x[j::c] (each spans the
+    whole id range, so every part touches every vertex region), each is
+    permuted uniformly, and the parts come in a random order."""
+    import torch
+    m = x.numel()
+    if m <= PERM_ONE:
+        yield x[torch.randperm(m, generator=gen, device=x.device)]
+        return
+    c = -(-m // PERM_CHUNK)
+    for j in torch.randperm(c, generator=gen, device=x.device).tolist():
+        sub = x[j::c]
+        yield sub[torch.randperm(sub.numel(), generator=gen, device=x.device)]
+
+
 def run_paper_streams(args):
     """The paper's stream shapes (§5 datasets, App. C) on Kronecker-shaped
     graphs of V = 2^levels at density 0.5 (workloads.kronecker_graph): the
@@ -1076,23 +1097,31 @@ def run_paper_streams(args):
         st, g = C.cupc_init(V, SEED, (0, 0, 0, 1 << 16), None, stream)
         C.check(st)
         stats = np.zeros(8, np.uint64)
+        fsorted = torch.sort(forest).values
         for shape in ("standard", "fixed_forest"):
             if shape == "standard":
-                seq = torch.cat([ids[torch.randperm(m, generator=gen, device=dev)],
-                                 ids[torch.randperm(m, generator=gen, device=dev)]])
-                ops = torch.cat([torch.ones(m, dtype=torch.int8, device=dev),
-                                 -torch.ones(m, dtype=torch.int8, device=dev)])
+                phases = [(ids, 1, True), (ids, -1, True)]
             else:
-                rest = ids[~torch.isin(ids, forest)]
-                k = rest.numel()
-                seq = torch.cat([forest, rest[torch.randperm(k, generator=gen, device=dev)],
-                                 rest[torch.randperm(k, generator=gen, device=dev)]])
-                ops = torch.cat([torch.ones(forest.numel() + k, dtype=torch.int8, device=dev),
-                                 -torch.ones(k, dtype=torch.int8, device=dev)])
+                keep = torch.ones(m, dtype=torch.bool, device=dev)
+                keep[torch.searchsorted(ids, fsorted)] = False
+                rest = torch.cat([ids[a:a + PERM_CHUNK][keep[a:a + PERM_CHUNK]] for a in range(0, m, PERM_CHUNK)])
+                del keep
+                phases = [(forest, 1, False), (rest, 1, True), (rest, -1, True)]
+            n = sum(x.numel() for x, _, _ in phases)
+            E = torch.empty((n, 2), dtype=torch.int32, device=dev)
+            ops = torch.empty(n, dtype=torch.int8, device=dev)
+            at = 0
+            for x, op, shuffle in phases:
+                for part in (shuffled_parts(x, gen) if shuffle else [x]):
+                    k = part.numel()
+                    E[at:at + k, 0] = (part // V).to(torch.int32)
+                    E[at:at + k, 1] = (part % V).to(torch.int32)
+                    ops[at:at + k] = op
+                    at += k
+                    del part
+            del phases
+            if shape == "fixed_forest":
                 del rest
-            n = seq.numel()
-            E = torch.stack([seq // V, seq % V], 1).to(torch.int32).contiguous()
-            del seq
             rng = WL.rng(17 + levels)
             rho = rng.integers(1000, 2001, size=n // 1000 + 2)
             starts = np.concatenate([[0], np.cumsum(rho)])
@@ -1100,7 +1129,10 @@ def run_paper_streams(args):
             starts = np.minimum(starts[:nb + 1], n)
             qn = np.maximum(1, (starts[1:] - starts[:-1]) // 9)
             qoff = np.concatenate([[0], np.cumsum(qn)])
-            P = torch.randint(0, V, (2 * int(qoff[-1]),), generator=gen, device=dev, dtype=torch.int32)
+            P = torch.empty(2 * int(qoff[-1]), dtype=torch.int32, device=dev)
+            for a in range(0, P.numel(), PERM_CHUNK):
+                b = min(P.numel(), a + PERM_CHUNK)
+                P[a:b] = torch.randint(0, V, (b - a,), generator=gen, device=dev, dtype=torch.int32)
             out = torch.empty(int(qoff[-1]), dtype=torch.uint8, device=dev)
             e_ptr, o_ptr, p_ptr, a_ptr = E.data_ptr(), ops.data_ptr(), P.data_ptr(), out.data_ptr()
             modes = (("incremental_labels", 1),) + ((("recovery_per_burst", 0),) if levels <= 13 else ())

@@ -403,7 +403,7 @@ __global__ void __launch_bounds__(256) k_plan_write(uint32_t* cnt, uint32_t* cur
         cursor[w] = pf;
         for (uint32_t q = 0; q < ni; q++) {
           const uint32_t bg = pf + q * item_records;
-          items[pi + q] = make_uint4(w, bg, min(pf + c, bg + item_records), ni == 1 ? 1u : 0u);
+          items[pi + q] = make_uint4(w, bg, min(pf + c, bg + item_records), 0u);
         }
       } else {
         cursor[w] = carry[1] + e[1];
@@ -479,7 +479,7 @@ __global__ void k_apply(ulonglong2* __restrict__ sketch, const uint64_t* __restr
       apply_direct<kLong>(l, sketch, V, W, rec + item.y, recw + item.y, item.z - item.y, L, m);
     } else {
       ulonglong2* gb = sketch + ((size_t)l.layer * V + item.x) * W + l.jbase;
-      apply_item<kLong>(l, gb, rec + item.y, item.z - item.y, item.w != 0, L, R, m, my_rows, rs);
+      apply_item<kLong>(l, gb, rec + item.y, item.z - item.y, L, R, m, my_rows, rs);
     }
     // both item paths end with __syncthreads: every thread has read s_item
     if (threadIdx.x == 0) s_item = gridDim.x + atomicAdd(&gc[GC_NEXT_ITEM], 1u);
