@@ -1170,7 +1170,9 @@ def run_paper_streams(args):
 
 def run_apply_profile(args):
     """Small cases for ncu. dense: a V=16384 graph (826 MB of sketches,
-    larger than L2) receives the first 8 insert batches of the dense stream.
+    larger than L2) receives the first 8 insert batches of the dense stream,
+    then one Connected batch (one grid-wide recovery). plain: the plain
+    V=1024 stream, 20 Connected batches (one-cluster recoveries).
     rmat: a V=2^15 graph (1.9 GB of sketches) receives 6 R-MAT batches of
     2^20..2^22 edges (the batched workload's generator at 15 levels)."""
     import torch
@@ -1178,6 +1180,24 @@ def run_apply_profile(args):
     from paper_2509_14433_gb300 import cupc as C
     torch.cuda.set_device(0)
     stream = torch.cuda.current_stream()
+    if args.profile_case == "plain":  # recoveries of the plain V=1024 stream (one-cluster kernel)
+        st, g = C.cupc_init(1024, SEED, None, None, stream)
+        C.check(st)
+        nq = 0
+        for kind, *rest in WL.plain_stream(V=1024, seed=1):
+            if kind == "update":
+                e, o = rest
+                C.check(C.cupc_update_batch(g, torch.from_numpy(e.reshape(-1)).cuda(), torch.from_numpy(o).cuda(),
+                                            len(o), stream))
+            else:
+                pr = rest[0]
+                out = torch.empty(len(pr), dtype=torch.uint8, device="cuda")
+                C.check(C.cupc_query(g, torch.from_numpy(pr.reshape(-1)).cuda(), len(pr), out, stream))
+                nq += 1
+        C.check(C.cupc_sync(g, stream))
+        C.cupc_destroy(g)
+        print("apply-profile plain done", nq, "queries")
+        return
     if args.profile_case == "rmat":
         V = 1 << 15
         s = WL.RmatStream(levels=15, seed=3, batch_lo=1 << 20, batch_hi=4 << 20, device="cuda")
@@ -1219,7 +1239,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batching", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
-    ap.add_argument("--profile-case", default="dense", choices=["dense", "rmat"])
+    ap.add_argument("--profile-case", default="dense", choices=["dense", "rmat", "plain"])
     args = ap.parse_args()
     if args.mode == "apply-profile":
         run_apply_profile(args)

@@ -77,6 +77,15 @@ constexpr uint32_t kWarpBuckets = 8;  // buckets per lane in the recovery: W <= 
 // Crossing candidates at or below which a recovery hook finishes in one CTA
 // (shared memory) instead of across the grid.
 constexpr uint32_t kSmallHook = 1024;
+// One-cluster recovery (recover_small.cu): graphs of at most kClMaxV
+// vertices keep their per-vertex recovery state in one CTA's shared memory
+// (26 bytes a vertex); kClThreads threads per CTA. Measured on GB300 (one
+// recovery after 100 toggles, ER graphs): V = 1024 58 us vs 118 us for the
+// grid-wide kernel, V = 2048 82 vs 128, V = 4096 140-168 vs 150-179; from
+// V = 6144 on the grid-wide kernel is faster (186 vs 157 us): the cluster's
+// 16 SMs run out of issue and memory bandwidth.
+constexpr uint32_t kClMaxV = 4096;
+constexpr uint32_t kClThreads = 512;
 // Bounded device-side waits give up after this long.
 constexpr uint64_t kWaitLimitNs = 2000000000ull;
 
@@ -160,6 +169,7 @@ struct cupc_graph {
     int smem, grid;
   } tune_b[16];
   int rec_grid;
+  int rec_cluster;  // CTAs of the one-cluster recovery (0: the grid-wide kernel)
   // sketches and keys
   ulonglong2* sketch;  // L*V*W
   uint64_t* keys;      // key_words(L, C)

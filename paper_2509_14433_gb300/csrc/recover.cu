@@ -27,32 +27,10 @@
 // A component whose merged sketch is ZERO has an empty cut; it is not sampled
 // again until it changes. With one live component left its merged sketch is
 // zero by linearity, so the round is logged without reading its layer.
-#include "common.cuh"
+#include "recover_dev.cuh"
 
 namespace cupc {
 
-struct RecArgs {
-  const ulonglong2* sketch;
-  const uint64_t* keys;
-  uint32_t V, L, C, D, W;
-  uint32_t *label, *parent, *minv, *rcnt, *roff, *perm, *permb, *pcount;
-  uint8_t *final_, *merged;
-  uint64_t *best0, *best1, *forest, *log_ids;
-  ulonglong2* cand;  // {edge, label[u] << 32 | label[v]} of a component's candidate
-  ulonglong2* acc;
-  uint32_t *log_live, *log_ncand;
-  ulonglong2* hlist;  // kSmallHook: crossing candidates {edge, root_a << 32 | root_b} of a hook step
-  uint32_t* ipar;     // V: union-find of incremental inserts, identity after a recovery
-  const uint64_t* forest_sorted;
-  uint8_t* fdead;     // V: forest_sorted[i] deleted since the last recovery
-  const uint64_t* fadd;      // V: forest edges added by incremental merges since
-  const uint8_t* fadd_dead;  // V: fadd[j] deleted since
-  unsigned long long* ftab;  // 2^ftab_bits: the ids of fadd (cleared here)
-  uint32_t ftab_bits;
-  uint32_t inc, force;  // incremental mode; run even if the labels are valid
-  uint32_t sum_zero;    // the XOR of all vertex sketches of a layer is zero (no import since reset)
-  uint32_t* gc;
-};
 
 // Grid barrier for a cooperative launch: CTA thread 0 adds one to an arrival
 // counter that only grows during the launch (the host zeroes it before) and
@@ -105,33 +83,6 @@ __device__ __forceinline__ uint32_t find_root(uint32_t* parent, uint32_t x, uint
   }
   if (r != x && ld_cg(&parent[x]) != r) parent[x] = r;
   return r;
-}
-
-// Sample a layer-r sum held by a warp (lane l holds buckets l + 32q): ZERO
-// if the deterministic bucket is zero, else the first good bucket in index
-// order (deterministic bucket, then column-major), else FAIL. Returns 0/1/2
-// in every lane and the edge id in `edge`. Buckets after the first good one
-// are not hashed (the flag is warp-uniform).
-__device__ __forceinline__ uint32_t warp_sample(const ulonglong2 (&acc)[kWarpBuckets], uint32_t W, uint32_t V,
-                                                uint64_t kchk, uint64_t& edge) {
-  const uint32_t lane = threadIdx.x & 31;
-  if (__shfl_sync(0xffffffffu, (acc[0].x | acc[0].y) == 0 ? 1u : 0u, 0)) return 0;
-  uint32_t found = 0;
-  uint64_t e = 0;
-#pragma unroll
-  for (uint32_t q = 0; q < kWarpBuckets; q++) {
-    const uint32_t j = lane + 32 * q;
-    bool good = false;
-    if (!found && j < W && acc[q].x != 0 && mix64(acc[q].x ^ kchk) == acc[q].y) good = acc[q].x / V < acc[q].x % V;
-    const uint32_t m = __ballot_sync(0xffffffffu, good);
-    const uint64_t x = __shfl_sync(0xffffffffu, acc[q].x, m ? __ffs(m) - 1 : 0);
-    if (!found && m) {
-      e = x;
-      found = 1;
-    }
-  }
-  edge = e;
-  return found ? 1u : 2u;
 }
 
 // Book the samples stashed in a warp, one per lane (K = kNoneU32: none):
@@ -192,19 +143,6 @@ __device__ __forceinline__ uint32_t warp_grab(uint32_t* ctr, uint32_t key, bool 
     pos = base + __popc(peers & ((1u << lane) - 1));
   }
   return pos;
-}
-
-__device__ __forceinline__ void warp_xor_row(ulonglong2 (&acc)[kWarpBuckets], const ulonglong2* __restrict__ row,
-                                             uint32_t W, uint32_t lane) {
-#pragma unroll
-  for (uint32_t q = 0; q < kWarpBuckets; q++) {
-    const uint32_t b = lane + 32 * q;
-    if (b < W) {
-      const ulonglong2 x = __ldg(row + b);
-      acc[q].x ^= x.x;
-      acc[q].y ^= x.y;
-    }
-  }
 }
 
 constexpr uint32_t kBigFlag = 0x80000000u;  // roff[K] flag: K's members are in permb
@@ -880,7 +818,7 @@ cudaError_t setup_recover(cupc_graph* g) {
   if (want < 16) want = 16;
   uint32_t cap = (uint32_t)(per_sm * g->sms);
   g->rec_grid = (int)(want < cap ? want : cap);
-  return cudaSuccess;
+  return setup_recover_cluster(g);
 }
 
 cudaError_t launch_recover(cupc_graph* g, cudaStream_t s, bool force) {
@@ -922,6 +860,10 @@ cudaError_t launch_recover(cupc_graph* g, cudaStream_t s, bool force) {
   a.force = force ? 1u : 0u;
   a.sum_zero = g->imported ? 0u : 1u;
   a.gc = g->gc;
+  if (g->rec_cluster) {
+    ProfScope ps(g, s, PC_RECOVER, 1);
+    return launch_recover_cluster(g, a, s);
+  }
   cudaError_t e = cudaMemsetAsync(g->gc + GC_BAR_COUNT, 0, sizeof(uint32_t), s);
   if (e != cudaSuccess) return e;
   ProfScope ps(g, s, PC_RECOVER, 1);

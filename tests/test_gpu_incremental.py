@@ -36,14 +36,16 @@ def _absent_pairs(V, k, present, g):
     return np.array(out, np.uint32)
 
 
-def test_incremental_labels_match_full_recovery():
+# V up to 4096 recovers in one thread-block cluster, larger V across the grid
+@pytest.mark.parametrize("V,p", [(1500, 0.0008), (5000, 0.00024)])
+def test_incremental_labels_match_full_recovery(V, p):
     from paper_2509_14433_gb300 import cupc as C
     from tests.test_gpu_parity import assert_same_recovery
-    V, seed = 1500, 31
+    seed = 31
     g = WL.rng(seed)
     dev, ref = _dev(V, seed), O.Graph(V, seed)
     assert C.cupc_set_incremental(dev.h, 1, None) == 0
-    E0 = WL.er_edges(V, 0.0008, seed)  # sparse: many components to merge
+    E0 = WL.er_edges(V, p, seed)  # sparse: many components to merge
     present = set(int(a) * V + int(b) for a, b in E0)
     assert dev.update(E0) == 0 and ref.update(E0) == O.OK
     queries = 0
@@ -99,24 +101,25 @@ def test_incremental_off_by_default_and_switchable():
     assert C.cupc_set_incremental(None, 1, None) == C.CUPC_EINVAL
 
 
-def test_warm_start_after_forest_edge_deletes():
+@pytest.mark.parametrize("V,p,per_batch", [(600, 0.02, 120), (5000, 0.0024, 1000)])
+def test_warm_start_after_forest_edge_deletes(V, p, per_batch):
     # delete-only batches: a deleted forest edge makes the next recovery
     # start from the fragments of the remaining forest (round 0 samples
     # fewer than V components); the graph falls apart over the batches and
     # every answer still equals the oracle's full recovery
     from paper_2509_14433_gb300 import cupc as C
     from tests.test_gpu_parity import assert_same_recovery
-    V, seed = 600, 41
+    seed = 41
     g = WL.rng(seed)
     dev, ref = _dev(V, seed), O.Graph(V, seed)
     assert C.cupc_set_incremental(dev.h, 1, None) == 0
-    E = WL.er_edges(V, 0.02, seed)
+    E = WL.er_edges(V, p, seed)
     present = set(int(a) * V + int(b) for a, b in E)
     assert dev.update(E) == 0 and ref.update(E) == O.OK
     warm = 0
     for k in range(25):
         ids = np.array(sorted(present), np.int64)
-        pick = ids[g.choice(len(ids), min(len(ids), 120), replace=False)]
+        pick = ids[g.choice(len(ids), min(len(ids), per_batch), replace=False)]
         present.difference_update(int(x) for x in pick)
         D = np.stack([pick // V, pick % V], 1).astype(np.uint32)
         ops = -np.ones(len(D), np.int8)
@@ -157,16 +160,17 @@ def test_fixed_forest_stream_keeps_the_labels():
     assert_same_recovery(dev, ref)
 
 
-def test_deleting_merge_edges_recovers_warm():
+@pytest.mark.parametrize("V,p", [(800, 0.002), (5000, 0.00032)])
+def test_deleting_merge_edges_recovers_warm(V, p):
     # inserts that join components become forest edges; deleting them (and
     # recovered forest edges) in a delete-only batch splits the components
     # again: the next query starts from the remaining fragments
     from paper_2509_14433_gb300 import cupc as C
-    V, seed = 800, 61
+    seed = 61
     g = WL.rng(seed)
     dev, ref = _dev(V, seed), O.Graph(V, seed)
     assert C.cupc_set_incremental(dev.h, 1, None) == 0
-    E0 = WL.er_edges(V, 0.002, seed)  # sparse: many components
+    E0 = WL.er_edges(V, p, seed)  # sparse: many components
     present = set(int(a) * V + int(b) for a, b in E0)
     assert dev.update(E0) == 0 and ref.update(E0) == O.OK
     pairs = WL.uniform_pairs(V, 500, g, distinct=False)

@@ -45,8 +45,10 @@ def assert_same_recovery(dev, ref):
         (os_["rounds"], os_["fail"], os_["false_pos"], os_["complete"])
 
 
+# V up to 4096 recovers in one thread-block cluster, larger V across the grid
 @pytest.mark.parametrize("V,p,seed", [(2, 1.0, 1), (5, 0.5, 2), (37, 0.2, 3), (256, 0.05, 4),
-                                       (1000, 0.01, 5), (1024, 0.5, 6), (3001, 0.002, 7)])
+                                       (1000, 0.01, 5), (1024, 0.5, 6), (3001, 0.002, 7), (4096, 0.01, 8),
+                                       (5000, 0.002, 9)])
 def test_sketches_and_recovery_bit_exact(V, p, seed):
     steps = WL.toggle_stream(V, WL.er_edges(V, p, seed), 3 * V, max(1, V // 2), 64, seed=seed + 10,
                              batch_cap=max(1, V * 7))
