@@ -12,7 +12,8 @@ four edges) and keeps the fastest; the table is stored as JSON keyed by GPU
 name and graph shape. apply() sets the setting of one batch size as a
 graph's default; apply_buckets() gives the graph every bucket's setting, and
 the library then picks one per batch by its size. Run `python -m paper_2509_14433_gb300.autotune --V 16384` on the
-target GPU to (re)write the table.
+target GPU to (re)write the table; `--batches rmat` times R-MAT batches (the
+degree skew of the batched R-MAT workload) instead of uniform ones.
 """
 from __future__ import annotations
 
@@ -119,9 +120,27 @@ def _time_setting(C, g, e_d, o_d, n, reps, setting):
     return float(ms[2]) / max(1, int(nl[2]))
 
 
-def tune(V: int, sizes=None, reps: int = 3, seed: int = 1, path: str = DEFAULT_CACHE, verbose: bool = True):
+RMAT_PROBS = (0.57, 0.19, 0.19, 0.05)
+
+
+def _batch(WL, V: int, n: int, rng, batches: str, gen):
+    """n edge pairs (uint32 [n, 2], u != v) on the device: uniform random, or
+    R-MAT (V a power of two; a self-loop's second end moves to the next id)."""
+    import torch
+    if batches == "rmat":
+        levels = V.bit_length() - 1
+        u, v = WL.rmat_pairs(n, levels, RMAT_PROBS, gen, "cuda")
+        v = torch.where(u == v, (v + 1) % V, v)
+        return torch.stack([u, v], 1).to(torch.int32).reshape(-1).contiguous()
+    return torch.from_numpy(WL.uniform_pairs(V, n, rng).reshape(-1)).cuda()
+
+
+def tune(V: int, sizes=None, reps: int = 3, seed: int = 1, path: str = DEFAULT_CACHE, verbose: bool = True,
+         batches: str = "uniform"):
     """Time every setting per batch-size bucket on a graph of V vertices
-    with uniform random batches; merge the winners into the JSON table."""
+    with uniform random or R-MAT batches (the degree skew of the batches
+    decides how many records a vertex gets); merge the winners into the
+    JSON table."""
     import torch
 
     from . import cupc as C
@@ -133,13 +152,15 @@ def tune(V: int, sizes=None, reps: int = 3, seed: int = 1, path: str = DEFAULT_C
     p = np.zeros(4, np.uint32)
     C.cupc_get_params(g, p)
     L, Cc, D, _ = (int(x) for x in p)
+    if batches == "rmat" and V & (V - 1):
+        raise ValueError("R-MAT batches need V a power of two")
     rng = WL.rng(seed)
+    gen = torch.Generator(device="cuda").manual_seed(seed)
     table = load(path)
     ent = table.setdefault(gpu_name(), {}).setdefault(shape_key(V, L, Cc, D), {})
     try:
         for n in sizes:
-            E = WL.uniform_pairs(V, n, rng)
-            e_d = torch.from_numpy(E.reshape(-1)).cuda()
+            e_d = _batch(WL, V, n, rng, batches, gen)
             o_d = torch.ones(n, dtype=torch.int8, device="cuda")
             results = []
             for it in ITEM_RECORDS:
@@ -154,7 +175,8 @@ def tune(V: int, sizes=None, reps: int = 3, seed: int = 1, path: str = DEFAULT_C
             best_t, best = results[0]
             default = [t for t, s in results if s == (256, min(8, D), 0)]
             ent[str(bucket_of(n))] = {"setting": list(best), "apply_ms": best_t,
-                                      "default_ms": default[0] if default else None, "edges": n}
+                                      "default_ms": default[0] if default else None, "edges": n,
+                                      "batches": batches}
             if verbose:
                 print(f"V={V} n={n}: best {best} {best_t:.4f} ms (default {default[0] if default else '-'} ms)",
                       flush=True)
@@ -172,10 +194,12 @@ def main():
     ap.add_argument("--max-edges", type=int, default=1 << 22)
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--out", default=DEFAULT_CACHE)
+    ap.add_argument("--batches", nargs="+", default=["uniform"], choices=["uniform", "rmat"],
+                    help="batch kind per --V entry (the last one repeats)")
     a = ap.parse_args()
-    for V in a.V:
+    for k, V in enumerate(a.V):
         sizes = [4 ** b for b in range(5, 12) if 4 ** b <= a.max_edges]
-        tune(V, sizes, reps=a.reps, path=a.out)
+        tune(V, sizes, reps=a.reps, path=a.out, batches=a.batches[min(k, len(a.batches) - 1)])
 
 
 if __name__ == "__main__":

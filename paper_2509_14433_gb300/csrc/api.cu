@@ -140,13 +140,14 @@ cupc_status from_cuda(cudaError_t e) {
     if (e_ != cudaSuccess) return from_cuda(e_); \
   } while (0)
 
-// Incremental mode keeps the forest sorted after every recovery: a batch's
-// deletes look up the forest (k_incr). The recovery returns at once while
-// the labels are valid, and the sort while the forest is sorted.
+// Incremental mode sorts the forest of a recovery before the next update
+// batch, whose deletes look it up (k_incr): the sort stays off the query's
+// path. The recovery returns at once while the labels are valid, and the
+// sort while the forest is sorted.
 cupc_status recover_if_dirty(cupc_graph* g, cudaStream_t s) {
   if (!g->dirty) return CUPC_OK;
   CUPC_TRY(launch_recover(g, s));
-  if (g->inc) CUPC_TRY(launch_forest_sort(g, s));
+  if (g->inc) g->sort_pending = true;
   g->dirty = false;
   return CUPC_OK;
 }

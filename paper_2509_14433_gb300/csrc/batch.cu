@@ -196,9 +196,9 @@ __global__ void k_apply_m(BatchHead* __restrict__ h, uint32_t rmax, uint32_t lma
     } else {
       ulonglong2* gb = g.sketch + ((size_t)l.layer * g.V + item.x) * g.W + l.jbase;
       if (g.long_depth)
-        apply_item<true>(l, gb, g.rec + item.y, item.z - item.y, g.L, g.R, m, my_rows, rs);
+        apply_item<true>(l, gb, g.rec + item.y, item.z - item.y, item.w != 0, g.L, g.R, m, my_rows, rs);
       else
-        apply_item<false>(l, gb, g.rec + item.y, item.z - item.y, g.L, g.R, m, my_rows, rs);
+        apply_item<false>(l, gb, g.rec + item.y, item.z - item.y, item.w != 0, g.L, g.R, m, my_rows, rs);
     }
     // both item paths end with __syncthreads: every thread has read s_item
     if (threadIdx.x == 0) s_item = gridDim.x + atomicAdd(&h->next_item, 1u);

@@ -47,6 +47,13 @@ constexpr uint32_t kPlanSlices = 1024;
 // Most CTAs of the single-graph apply kernel (its direct-path items number
 // at most 2 per CTA + 1 beyond one per 64 direct records).
 constexpr uint32_t kPlanGridCap = 8192;
+// Below this many endpoint records per vertex on average in a batch, the
+// apply kernel writes a single-item vertex back by load and store; at or
+// above it, by XOR atomics. GB300, uniform batches, ms per launch
+// (load-store / atomics): V = 2^17 and 2^18, 2^20, 2^22 edges: 1.03 / 1.25,
+// 1.47 / 1.62, 2.84 / 2.29; V = 16384 and 2^16, 2^18, 2^20 edges: 0.14 /
+// 0.18, 0.21 / 0.21, 0.48 / 0.41.
+constexpr uint32_t kExclRecords = 32;
 // Records an apply CTA stages per pass: idx and the checksums G_r(idx) of
 // every layer of kStage records sit in shared memory.
 constexpr uint32_t kStage = 64;
@@ -157,6 +164,7 @@ struct cupc_graph {
   bool dirty;
   bool inc;           // incremental labels (cupc_set_incremental)
   bool forest_stale;  // an update since the last full recovery
+  bool sort_pending;  // incremental mode: a recovery ran; the next update sorts its forest first
   bool imported;      // words from cupc_import_sketches since the last reset:
                       // the XOR of all vertex sketches need not be zero
   int device, sms;

@@ -28,6 +28,9 @@
 // Control flow is uniform over the cluster: the leader decides whether a
 // round runs and publishes that in gc[GC_ACTIVE] before a cluster barrier;
 // every CTA reads it after the barrier, so all CTAs pass the same barriers.
+// The barrier's arrive has release and its wait acquire semantics at
+// cluster scope, which order the global writes of one CTA before the reads
+// of another; data written by another CTA is read through L2 (ld.cg).
 #include "recover_dev.cuh"
 
 namespace cupc {
@@ -388,9 +391,8 @@ __global__ void __launch_bounds__(kClThreads, 1) k_recover_cl(RecArgs a) {
         gc[GC_NMEMBERS] = n;
         gc[GC_ACTIVE] = stop ? 0u : (multi ? 2u : 1u);
       }
-      __threadfence();
     }
-    cluster_sync_all();
+    cluster_sync_all();  // release/acquire at cluster scope: the groups and gc words are visible
     const uint32_t ctl = ld_cg(&gc[GC_ACTIVE]);
     if (ctl == 0) break;
     const uint32_t n = ld_cg(&gc[GC_NMEMBERS]);
@@ -480,8 +482,7 @@ __global__ void __launch_bounds__(kClThreads, 1) k_recover_cl(RecArgs a) {
         }
       }
     }
-    __threadfence();
-    cluster_sync_all();
+    cluster_sync_all();  // the samples in cand are visible to the leader
     if (!leader) continue;
     // ---- book the samples of the live components
     for (uint32_t K = tid; K < V; K += nt) {

@@ -304,6 +304,11 @@ __global__ void k_incr_finish(uint32_t* label, uint32_t* ipar, uint32_t V, uint3
 
 cudaError_t launch_incremental(cupc_graph* g, const uint32_t* edges, const int8_t* ops, size_t n, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
+  if (g->sort_pending) {  // the forest of the last recovery, which this batch's deletes look up
+    cudaError_t e = launch_forest_sort(g, s);
+    if (e != cudaSuccess) return e;
+    g->sort_pending = false;
+  }
   cudaError_t e = cudaMemsetAsync(g->gc + GC_BATCH_DEL, 0, sizeof(uint32_t), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(g->gc + GC_BATCH_MERGE, 0, sizeof(uint32_t), s);
   if (e != cudaSuccess) return e;
@@ -403,7 +408,7 @@ __global__ void __launch_bounds__(256) k_plan_write(uint32_t* cnt, uint32_t* cur
         cursor[w] = pf;
         for (uint32_t q = 0; q < ni; q++) {
           const uint32_t bg = pf + q * item_records;
-          items[pi + q] = make_uint4(w, bg, min(pf + c, bg + item_records), 0u);
+          items[pi + q] = make_uint4(w, bg, min(pf + c, bg + item_records), ni == 1 ? 1u : 0u);
         }
       } else {
         cursor[w] = carry[1] + e[1];
@@ -449,8 +454,10 @@ __global__ void k_scatter(const uint32_t* __restrict__ edges, size_t n, uint32_t
 }
 
 // Fold the records of one work item into the sketches of its vertex (see
-// apply_item); persistent CTAs pull work items from a counter.
-template <bool kLong>
+// apply_item); persistent CTAs pull work items from a counter. kExcl: a
+// vertex with a single item writes back by load and store, else every
+// write-back is by XOR atomics (the launch picks by records per vertex).
+template <bool kLong, bool kExcl>
 __global__ void k_apply(ulonglong2* __restrict__ sketch, const uint64_t* __restrict__ keys,
                         const uint64_t* __restrict__ rec, const uint32_t* __restrict__ recw,
                         const uint4* __restrict__ items, uint32_t* gc, uint32_t V, uint32_t L, uint32_t C,
@@ -479,7 +486,7 @@ __global__ void k_apply(ulonglong2* __restrict__ sketch, const uint64_t* __restr
       apply_direct<kLong>(l, sketch, V, W, rec + item.y, recw + item.y, item.z - item.y, L, m);
     } else {
       ulonglong2* gb = sketch + ((size_t)l.layer * V + item.x) * W + l.jbase;
-      apply_item<kLong>(l, gb, rec + item.y, item.z - item.y, L, R, m, my_rows, rs);
+      apply_item<kLong>(l, gb, rec + item.y, item.z - item.y, kExcl && item.w != 0, L, R, m, my_rows, rs);
     }
     // both item paths end with __syncthreads: every thread has read s_item
     if (threadIdx.x == 0) s_item = gridDim.x + atomicAdd(&gc[GC_NEXT_ITEM], 1u);
@@ -492,7 +499,8 @@ __global__ void k_apply(ulonglong2* __restrict__ sketch, const uint64_t* __restr
 // raise it, so that a graph created later never shrinks it below what an
 // earlier graph's launches need.
 cudaError_t raise_apply_smem_limit(int bytes) {
-  const void* fns[2] = {(const void*)k_apply<false>, (const void*)k_apply<true>};
+  const void* fns[4] = {(const void*)k_apply<false, false>, (const void*)k_apply<true, false>,
+                        (const void*)k_apply<false, true>, (const void*)k_apply<true, true>};
   for (const void* f : fns) {
     cudaFuncAttributes fa;
     cudaError_t e = cudaFuncGetAttributes(&fa, f);
@@ -527,7 +535,8 @@ cudaError_t apply_config(const cupc_graph* g, uint32_t item_records, uint32_t R,
   cudaError_t e = raise_apply_smem_limit(*smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, g->long_depth ? k_apply<true> : k_apply<false>,
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm,
+                                                    g->long_depth ? k_apply<true, false> : k_apply<false, false>,
                                                     g->apply_threads, *smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
@@ -579,7 +588,12 @@ cudaError_t launch_update_chunk(cupc_graph* g, const uint32_t* edges, size_t n, 
       k_scatter<<<grid, 256, 0, s>>>(edges, n, g->V, g->cursor, g->rec, g->recw, g->gc);
   }
   ProfScope ps(g, s, PC_APPLY, 1);
-  auto kern = g->long_depth ? k_apply<true> : k_apply<false>;
+  // fewer than kExclRecords endpoint records per vertex on average: most
+  // touched rows hold one or two records, and a load-then-store write-back
+  // of a vertex's single item beats atomics (measured on GB300)
+  const bool excl = 2 * n < (size_t)kExclRecords * g->V;
+  auto kern = g->long_depth ? (excl ? k_apply<true, true> : k_apply<true, false>)
+                            : (excl ? k_apply<false, true> : k_apply<false, false>);
   kern<<<agrid, g->apply_threads, smem, s>>>(g->sketch, g->keys, g->rec, g->recw, g->items, g->gc, g->V, g->L, g->C,
                                               g->D, g->W, g->P, R, g->ell);
   return cudaGetLastError();
@@ -590,7 +604,7 @@ cudaError_t launch_update_chunk(cupc_graph* g, const uint32_t* edges, size_t n, 
 extern "C" cupc_status cupc_build_info(int* binary_version, int* ptx_version) {
   if (!binary_version || !ptx_version) return CUPC_EINVAL;
   cudaFuncAttributes fa;
-  if (cudaFuncGetAttributes(&fa, (const void*)cupc::k_apply<false>) != cudaSuccess) {
+  if (cudaFuncGetAttributes(&fa, (const void*)cupc::k_apply<false, false>) != cudaSuccess) {
     cudaGetLastError();
     return CUPC_ECUDA;
   }

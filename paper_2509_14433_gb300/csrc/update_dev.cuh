@@ -57,9 +57,10 @@ constexpr uint32_t kDirectItemMin = 16;      // sizes them to the apply grid
 
 // Work plan of one batch, run by one CTA: vertices with more than
 // kDirectMax records ("fold" vertices) get record segments after all direct
-// records and ceil(n_w / item_records) items {w, begin, end, 0}; direct
-// vertices' records come first and are cut into items of item_records
-// records {kDirectItem, begin, end, 0}. Writes the per-vertex
+// records and ceil(n_w / item_records) items {w, begin, end, exclusive}
+// (exclusive: the vertex has a single item, so no other CTA writes its
+// buckets); direct vertices' records come first and are cut into items of
+// item_records records {kDirectItem, begin, end, 0}. Writes the per-vertex
 // scatter cursors, resets cnt, returns the item count and the number of
 // direct records (*nd). Direct items hold kDirectItemRecords records.
 __device__ __forceinline__ uint32_t plan_vertices(uint32_t* cnt, uint32_t* cursor, uint4* items, uint32_t V,
@@ -106,7 +107,7 @@ __device__ __forceinline__ uint32_t plan_vertices(uint32_t* cnt, uint32_t* curso
         cursor[w] = pf;
         for (uint32_t q = 0; q < ni; q++) {
           const uint32_t b = pf + q * item_records;
-          items[pi + q] = make_uint4(w, b, min(pf + c[k], b + item_records), 0u);
+          items[pi + q] = make_uint4(w, b, min(pf + c[k], b + item_records), ni == 1 ? 1u : 0u);
         }
         pf += c[k];
         pi += ni;
@@ -305,11 +306,12 @@ __device__ __forceinline__ void fold_pair(ulonglong2* gb, ulonglong2* my_rows, u
 // (rs = blockDim.x), so the lanes of a shared-memory phase hit distinct
 // 16-byte bank groups; a lane is the only writer of its rows, so no shared
 // atomics are needed. Four records at a time: their loads and depths are
-// independent, and they fold as two overlapping pairs. Call from every
-// thread.
+// independent, and they fold as two overlapping pairs. `excl`: no other CTA
+// writes this vertex, so the write-back may be a plain read-modify-write.
+// Call from every thread.
 template <bool kLong>
 __device__ __forceinline__ void apply_item(const ApplyLane& l, ulonglong2* gb, const uint64_t* __restrict__ rec,
-                                           uint32_t n, uint32_t L, uint32_t R, const ApplySmem& m,
+                                           uint32_t n, bool excl, uint32_t L, uint32_t R, const ApplySmem& m,
                                            ulonglong2* my_rows, uint32_t rs) {
   const uint32_t cs = stage_size(), tid = threadIdx.x;
   const uint64_t* gcol = m.g + l.layer;
@@ -339,20 +341,45 @@ __device__ __forceinline__ void apply_item(const ApplyLane& l, ulonglong2* gb, c
     }
   }
 
-  // write back only the touched (non-zero) rows of this vertex, with
-  // fire-and-forget XOR atomics: a lane never waits for the old bucket (a
-  // load-then-store write-back was 10-15 % slower for that wait), and the
-  // items of a vertex split over several CTAs need nothing else
+  // write back only the touched (non-zero) rows of this vertex. excl (the
+  // vertex has this one item): load the old buckets, store the XOR; else
+  // fire-and-forget XOR atomics, where a lane never waits for the old
+  // bucket. Atomics are faster where vertices receive many records per
+  // batch (fewer, hotter rows); load-then-store where they receive few.
   if (l.active) {
-    for (uint32_t d0 = 0; d0 < l.nrows; d0 += 4) {
+    if (excl) {
+      for (uint32_t d0 = 0; d0 < l.nrows; d0 += 4) {
+        ulonglong2 v[4], o[4];
+        bool nz[4];
 #pragma unroll
-      for (uint32_t q = 0; q < 4; q++) {
-        const uint32_t d = d0 + q;
-        if (d < l.nrows) {
-          const ulonglong2 w = my_rows[d * rs];
-          if ((w.x | w.y) != 0) {
-            my_rows[d * rs] = make_ulonglong2(0, 0);
-            xor_bucket_atomic(gb + d, w);
+        for (uint32_t q = 0; q < 4; q++) {
+          const uint32_t d = d0 + q;
+          v[q] = make_ulonglong2(0, 0);
+          nz[q] = false;
+          if (d < l.nrows) {
+            v[q] = my_rows[d * rs];
+            nz[q] = (v[q].x | v[q].y) != 0;
+            if (nz[q]) my_rows[d * rs] = make_ulonglong2(0, 0);
+          }
+        }
+#pragma unroll
+        for (uint32_t q = 0; q < 4; q++)
+          if (nz[q]) o[q] = __ldcg(gb + d0 + q);
+#pragma unroll
+        for (uint32_t q = 0; q < 4; q++)
+          if (nz[q]) gb[d0 + q] = make_ulonglong2(o[q].x ^ v[q].x, o[q].y ^ v[q].y);
+      }
+    } else {
+      for (uint32_t d0 = 0; d0 < l.nrows; d0 += 4) {
+#pragma unroll
+        for (uint32_t q = 0; q < 4; q++) {
+          const uint32_t d = d0 + q;
+          if (d < l.nrows) {
+            const ulonglong2 w = my_rows[d * rs];
+            if ((w.x | w.y) != 0) {
+              my_rows[d * rs] = make_ulonglong2(0, 0);
+              xor_bucket_atomic(gb + d, w);
+            }
           }
         }
       }

@@ -160,3 +160,6 @@ def test_autotuner_writes_a_table_and_applies_it(tmp_path):
     out = np.zeros(4, np.uint32)
     C.cupc_get_tuning(dev.h, out)
     assert list(int(x) for x in out[:3]) == ent["8"]["setting"]
+    # R-MAT batches (the skewed-degree workload) fill the same table
+    ent2 = AT.tune(2048, sizes=[4096], reps=1, path=path, verbose=False, batches="rmat")
+    assert ent2["6"]["batches"] == "rmat" and ent2["8"]["batches"] == "uniform"
