@@ -277,6 +277,15 @@ cupc_status cupc_get_tuning(const cupc_graph* g, uint32_t* out4);
  * clear the bucket. CUPC_EINVAL when out of range. */
 cupc_status cupc_set_tuning_bucket(cupc_graph* g, uint32_t bucket, uint32_t item_records, uint32_t smem_rows,
                                    uint32_t ctas_per_sm);
+/* Write-back of a vertex whose records form a single work item, for one
+ * batch-size bucket (5..15, as above): CUPC_WRITEBACK_AUTO = load-and-store
+ * when the chunk averages fewer than 32 endpoint records per vertex, else
+ * XOR atomics (the default); CUPC_WRITEBACK_LOAD_STORE and
+ * CUPC_WRITEBACK_ATOMIC force one. Vertices split over several items always
+ * write back by atomics. Results are identical for every mode.
+ * CUPC_EINVAL when bucket or mode is out of range. */
+enum { CUPC_WRITEBACK_AUTO = 0, CUPC_WRITEBACK_LOAD_STORE = 1, CUPC_WRITEBACK_ATOMIC = 2 };
+cupc_status cupc_set_writeback_bucket(cupc_graph* g, uint32_t bucket, uint32_t mode);
 
 /* Derived parameters of a graph: out4 = {L, C, D, W}. */
 cupc_status cupc_get_params(const cupc_graph* g, uint32_t* out4);

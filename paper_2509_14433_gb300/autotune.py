@@ -8,7 +8,9 @@ records a vertex receives per batch, i.e. on V and the batch size.
 
 tune() times every candidate setting on the device (CUDA events recorded by
 the library around each apply launch) for each batch-size bucket (powers of
-four edges) and keeps the fastest; the table is stored as JSON keyed by GPU
+four edges) and keeps the fastest, then times the write-back of single-item
+vertices both ways (load-and-store, XOR atomics) with it and keeps the
+faster; the table is stored as JSON keyed by GPU
 name and graph shape. apply() sets the setting of one batch size as a
 graph's default; apply_buckets() gives the graph every bucket's setting, and
 the library then picks one per batch by its size. Run `python -m paper_2509_14433_gb300.autotune --V 16384` on the
@@ -56,9 +58,7 @@ def load(path: str = DEFAULT_CACHE) -> dict:
         return {}
 
 
-def lookup(table: dict, V: int, L: int, C: int, D: int, n_edges: int):
-    """(item_records, smem_rows, ctas_per_sm) for this GPU, shape and batch
-    size, or None (defaults stay)."""
+def _entry(table: dict, V: int, L: int, C: int, D: int, n_edges: int):
     try:
         import torch
         name = torch.cuda.get_device_name(0)
@@ -69,8 +69,14 @@ def lookup(table: dict, V: int, L: int, C: int, D: int, n_edges: int):
         return None
     b = bucket_of(n_edges)
     keys = sorted(int(k) for k in ent)
-    best = min(keys, key=lambda k: abs(k - b))
-    return tuple(ent[str(best)]["setting"])
+    return ent[str(min(keys, key=lambda k: abs(k - b)))]
+
+
+def lookup(table: dict, V: int, L: int, C: int, D: int, n_edges: int):
+    """(item_records, smem_rows, ctas_per_sm) for this GPU, shape and batch
+    size, or None (defaults stay)."""
+    e = _entry(table, V, L, C, D, n_edges)
+    return None if e is None else tuple(e["setting"])
 
 
 def apply(g, V: int, n_edges: int, table: dict | None = None) -> bool:
@@ -79,10 +85,12 @@ def apply(g, V: int, n_edges: int, table: dict | None = None) -> bool:
     p = np.zeros(4, np.uint32)
     C.cupc_get_params(g, p)
     L, Cc, D, _ = (int(x) for x in p)
-    s = lookup(load() if table is None else table, V, L, Cc, D, n_edges)
-    if s is None:
+    e = _entry(load() if table is None else table, V, L, Cc, D, n_edges)
+    if e is None:
         return False
-    return C.cupc_set_tuning(g, *s) == C.CUPC_OK
+    if "writeback" in e:
+        C.check(C.cupc_set_writeback_bucket(g, bucket_of(n_edges), int(e["writeback"])))
+    return C.cupc_set_tuning(g, *e["setting"]) == C.CUPC_OK
 
 
 def apply_buckets(g, V: int, table: dict | None = None) -> int:
@@ -103,11 +111,15 @@ def apply_buckets(g, V: int, table: dict | None = None) -> int:
     for b, e in ent.items():
         if 5 <= int(b) <= 15 and C.cupc_set_tuning_bucket(g, int(b), *e["setting"]) == C.CUPC_OK:
             k += 1
+            if "writeback" in e:
+                C.check(C.cupc_set_writeback_bucket(g, int(b), int(e["writeback"])))
     return k
 
 
-def _time_setting(C, g, e_d, o_d, n, reps, setting):
+def _time_setting(C, g, e_d, o_d, n, reps, setting, writeback=0):
     if C.cupc_set_tuning(g, *setting) != C.CUPC_OK:
+        return None
+    if C.cupc_set_writeback_bucket(g, bucket_of(n), writeback) != C.CUPC_OK:
         return None
     C.check(C.cupc_update_batch(g, e_d, o_d, n, None))  # warm
     C.cupc_profile_enable(g, 1)
@@ -174,12 +186,18 @@ def tune(V: int, sizes=None, reps: int = 3, seed: int = 1, path: str = DEFAULT_C
             results.sort()
             best_t, best = results[0]
             default = [t for t, s in results if s == (256, min(8, D), 0)]
-            ent[str(bucket_of(n))] = {"setting": list(best), "apply_ms": best_t,
+            # the write-back of single-item vertices, forced each way, for the best setting
+            wb_t = {m: _time_setting(C, g, e_d, o_d, n, reps, best, m)
+                    for m in (C.CUPC_WRITEBACK_LOAD_STORE, C.CUPC_WRITEBACK_ATOMIC)}
+            wb = min(wb_t, key=lambda m: wb_t[m])
+            C.cupc_set_writeback_bucket(g, bucket_of(n), C.CUPC_WRITEBACK_AUTO)
+            ent[str(bucket_of(n))] = {"setting": list(best), "apply_ms": min(best_t, wb_t[wb]),
                                       "default_ms": default[0] if default else None, "edges": n,
-                                      "batches": batches}
+                                      "batches": batches, "writeback": wb,
+                                      "writeback_ms": {str(m): t for m, t in wb_t.items()}}
             if verbose:
-                print(f"V={V} n={n}: best {best} {best_t:.4f} ms (default {default[0] if default else '-'} ms)",
-                      flush=True)
+                print(f"V={V} n={n}: best {best} {best_t:.4f} ms (default {default[0] if default else '-'} ms), "
+                      f"write-back load-store {wb_t[1]:.4f} / atomic {wb_t[2]:.4f} ms", flush=True)
     finally:
         C.cupc_destroy(g)
     with open(path + ".tmp", "w") as f:

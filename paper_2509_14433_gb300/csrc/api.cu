@@ -586,6 +586,12 @@ cupc_status cupc_set_tuning_bucket(cupc_graph* g, uint32_t bucket, uint32_t item
   return CUPC_OK;
 }
 
+cupc_status cupc_set_writeback_bucket(cupc_graph* g, uint32_t bucket, uint32_t mode) {
+  if (!g || bucket < 5 || bucket > 15 || mode > CUPC_WRITEBACK_ATOMIC) return CUPC_EINVAL;
+  g->wb_b[bucket] = mode;
+  return CUPC_OK;
+}
+
 cupc_status cupc_get_tuning(const cupc_graph* g, uint32_t* out4) {
   if (!g || !out4) return CUPC_EINVAL;
   out4[0] = g->item_records;

@@ -176,6 +176,7 @@ struct cupc_graph {
     uint32_t item_records, R, cps;
     int smem, grid;
   } tune_b[16];
+  uint32_t wb_b[16];  // write-back mode per bucket (CUPC_WRITEBACK_*)
   int rec_grid;
   int rec_cluster;  // CTAs of the one-cluster recovery (0: the grid-wide kernel)
   // sketches and keys

@@ -586,6 +586,11 @@ __global__ void __launch_bounds__(kRecThreads, 2) k_recover(RecArgs a) {
         mw = multi ? ld_cg(&a.perm[i0 + lane]) : i0 + lane;
         mk = multi ? ld_cg(&a.label[mw]) : mw;
       }
+      if (multi && lane < cnt) {  // every member's row heads for L2 while the first ones fold
+        const ulonglong2* row = a.sketch + ((size_t)r * V + mw) * W;
+        for (uint32_t b = 0; b < W; b += 8) asm volatile("prefetch.global.L2 [%0];" ::"l"(row + b));
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(row + W - 1));
+      }
       uint32_t i = 0;
       while (i < cnt) {
         const uint32_t K = __shfl_sync(0xffffffffu, mk, i);

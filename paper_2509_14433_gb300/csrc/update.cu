@@ -588,10 +588,11 @@ cudaError_t launch_update_chunk(cupc_graph* g, const uint32_t* edges, size_t n, 
       k_scatter<<<grid, 256, 0, s>>>(edges, n, g->V, g->cursor, g->rec, g->recw, g->gc);
   }
   ProfScope ps(g, s, PC_APPLY, 1);
-  // fewer than kExclRecords endpoint records per vertex on average: most
-  // touched rows hold one or two records, and a load-then-store write-back
-  // of a vertex's single item beats atomics (measured on GB300)
-  const bool excl = 2 * n < (size_t)kExclRecords * g->V;
+  // the bucket's write-back mode; by default load-then-store for a vertex's
+  // single item when the chunk averages fewer than kExclRecords endpoint
+  // records per vertex (most touched rows then hold one or two records)
+  const uint32_t wb = g->wb_b[tune_bucket(n)];
+  const bool excl = wb == CUPC_WRITEBACK_AUTO ? 2 * n < (size_t)kExclRecords * g->V : wb == CUPC_WRITEBACK_LOAD_STORE;
   auto kern = g->long_depth ? (excl ? k_apply<true, true> : k_apply<true, false>)
                             : (excl ? k_apply<false, true> : k_apply<false, false>);
   kern<<<agrid, g->apply_threads, smem, s>>>(g->sketch, g->keys, g->rec, g->recw, g->items, g->gc, g->V, g->L, g->C,

@@ -46,6 +46,7 @@ _SIGS = {
     "cupc_get_params": (ctypes.c_int, [_P, _P]),
     "cupc_set_tuning": (ctypes.c_int, [_P, _u32, _u32, _u32]),
     "cupc_set_tuning_bucket": (ctypes.c_int, [_P, _u32, _u32, _u32, _u32]),
+    "cupc_set_writeback_bucket": (ctypes.c_int, [_P, _u32, _u32]),
     "cupc_set_incremental": (ctypes.c_int, [_P, ctypes.c_int, _P]),
     "cupc_update_batches": (ctypes.c_int, [_P, _P, _P, _P, _sz, _P]),
     "cupc_batcher_create": (ctypes.c_int, [_u32, ctypes.c_int, _P]),
@@ -264,6 +265,10 @@ def cupc_set_tuning_bucket(g, bucket: int, item_records: int, smem_rows: int, ct
     return _lib.cupc_set_tuning_bucket(g, bucket, item_records, smem_rows, ctas_per_sm)
 
 
+def cupc_set_writeback_bucket(g, bucket: int, mode: int) -> int:
+    return _lib.cupc_set_writeback_bucket(g, bucket, mode)
+
+
 def cupc_set_incremental(g, on: int, stream=None) -> int:
     return _lib.cupc_set_incremental(g, on, stream_handle(stream))
 
@@ -289,6 +294,7 @@ def cupc_selftest_wait_timeout(ctas: int, limit_us: int, absent_cta: int, stream
 
 
 CUPC_CUTSET_LINK, CUPC_CUTSET_CUT, CUPC_CUTSET_REFRESH = 1, 2, 3
+CUPC_WRITEBACK_AUTO, CUPC_WRITEBACK_LOAD_STORE, CUPC_WRITEBACK_ATOMIC = 0, 1, 2
 
 
 def cupc_cutset_create(g, stream=None):

@@ -63,4 +63,5 @@ def test_status_strings_and_null_handles(C):
     assert C.cupc_update_batch(None, None, None, 0) == C.CUPC_EINVAL
     assert C.cupc_sync(None) == C.CUPC_EINVAL
     assert C.cupc_init(1, 0)[0] == C.CUPC_EINVAL
+    assert C.cupc_set_writeback_bucket(None, 10, C.CUPC_WRITEBACK_ATOMIC) == C.CUPC_EINVAL
     C.cupc_destroy(None)

@@ -145,6 +145,19 @@ def test_every_tuning_gives_identical_sketches():
     assert C.cupc_set_tuning_bucket(dev.h, 6, 32, 8, 0) == C.CUPC_EINVAL
     assert C.cupc_set_tuning(dev.h, 32, 12, 0) == C.CUPC_EINVAL  # records per item below 64
     assert C.cupc_set_tuning(dev.h, 512, 17, 0) == C.CUPC_EINVAL  # more than 16 shared rows
+    # both write-backs of single-item vertices, forced per bucket, and the automatic choice
+    for mode in (C.CUPC_WRITEBACK_LOAD_STORE, C.CUPC_WRITEBACK_ATOMIC, C.CUPC_WRITEBACK_AUTO):
+        dev = _dev(V, 8)
+        for b in range(5, 16):
+            assert C.cupc_set_writeback_bucket(dev.h, b, mode) == 0
+        i = 0
+        for n in (1000, 5000, 20000, 3):
+            assert dev.update(E[i:i + n]) == 0
+            i += n
+        assert dev.update(E[i:]) == 0
+        assert np.array_equal(dev.export(), want), mode
+    assert C.cupc_set_writeback_bucket(dev.h, 4, C.CUPC_WRITEBACK_ATOMIC) == C.CUPC_EINVAL
+    assert C.cupc_set_writeback_bucket(dev.h, 10, 3) == C.CUPC_EINVAL
     assert AT.bucket_of(1000) == 5 and AT.bucket_of(4096) == 6 and AT.bucket_of(1 << 20) == 10
 
 
@@ -163,3 +176,5 @@ def test_autotuner_writes_a_table_and_applies_it(tmp_path):
     # R-MAT batches (the skewed-degree workload) fill the same table
     ent2 = AT.tune(2048, sizes=[4096], reps=1, path=path, verbose=False, batches="rmat")
     assert ent2["6"]["batches"] == "rmat" and ent2["8"]["batches"] == "uniform"
+    assert ent2["6"]["writeback"] in (C.CUPC_WRITEBACK_LOAD_STORE, C.CUPC_WRITEBACK_ATOMIC)
+    assert AT.apply_buckets(dev.h, 2048, AT.load(path)) == 2
