@@ -87,12 +87,13 @@ constexpr uint32_t kSmallHook = 1024;
 // One-cluster recovery (recover_small.cu): graphs of at most kClMaxV
 // vertices keep their per-vertex recovery state in one CTA's shared memory
 // (26 bytes a vertex); kClThreads threads per CTA. Measured on GB300 (one
-// recovery after 100 toggles, ER graphs): V = 1024 58 us vs 118 us for the
-// grid-wide kernel, V = 2048 82 vs 128, V = 4096 140-168 vs 150-179; from
-// V = 6144 on the grid-wide kernel is faster (186 vs 157 us): the cluster's
-// 16 SMs run out of issue and memory bandwidth.
+// recovery after 100 toggles, ER graphs): V = 1024 55 us vs 118 us for the
+// grid-wide kernel, V = 2048 74 vs 128, V = 4096 117-148 vs 150-179 (1024
+// threads per CTA; 512 gave 56, 81 and 139-167 us). With 512 threads the
+// grid-wide kernel was faster from V = 6144 on (186 vs 157 us): the
+// cluster's 16 SMs run out of issue and memory bandwidth.
 constexpr uint32_t kClMaxV = 4096;
-constexpr uint32_t kClThreads = 512;
+constexpr uint32_t kClThreads = 1024;
 // Bounded device-side waits give up after this long.
 constexpr uint64_t kWaitLimitNs = 2000000000ull;
 

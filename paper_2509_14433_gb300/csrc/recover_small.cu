@@ -102,7 +102,8 @@ __device__ __forceinline__ uint32_t cl_find(volatile uint32_t* par, uint32_t x, 
   return x;
 }
 
-// Block-wide sum of a per-thread value (every thread gets it).
+// Block-wide sum of a per-thread value (every thread gets it). s_red: 32
+// words per summed value.
 __device__ __forceinline__ uint32_t block_sum(uint32_t v, uint32_t* s_red) {
   const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   v = __reduce_add_sync(0xffffffffu, v);
@@ -111,6 +112,27 @@ __device__ __forceinline__ uint32_t block_sum(uint32_t v, uint32_t* s_red) {
   __syncthreads();
   uint32_t t = lane < nw ? s_red[lane] : 0;
   return __reduce_add_sync(0xffffffffu, t);
+}
+
+// Four block-wide sums behind one pair of barriers.
+__device__ __forceinline__ uint4 block_sum4(uint4 v, uint32_t* s_red) {
+  const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  v.x = __reduce_add_sync(0xffffffffu, v.x);
+  v.y = __reduce_add_sync(0xffffffffu, v.y);
+  v.z = __reduce_add_sync(0xffffffffu, v.z);
+  v.w = __reduce_add_sync(0xffffffffu, v.w);
+  __syncthreads();
+  if (lane == 0) {
+    s_red[wid] = v.x;
+    s_red[32 + wid] = v.y;
+    s_red[64 + wid] = v.z;
+    s_red[96 + wid] = v.w;
+  }
+  __syncthreads();
+  uint4 t = make_uint4(0, 0, 0, 0);
+  if (lane < nw) t = make_uint4(s_red[lane], s_red[32 + lane], s_red[64 + lane], s_red[96 + lane]);
+  return make_uint4(__reduce_add_sync(0xffffffffu, t.x), __reduce_add_sync(0xffffffffu, t.y),
+                    __reduce_add_sync(0xffffffffu, t.z), __reduce_add_sync(0xffffffffu, t.w));
 }
 
 // Leader: group the members of the live components (label not final) by
@@ -261,7 +283,7 @@ __device__ void cl_hook(const RecArgs& a, const ClSmem& m, uint32_t V, uint32_t 
 template <uint32_t NQ>
 __global__ void __launch_bounds__(kClThreads, 1) k_recover_cl(RecArgs a) {
   extern __shared__ __align__(16) unsigned char cl_dyn[];
-  __shared__ uint32_t s_red[32];
+  __shared__ uint32_t s_red[128];
   __shared__ uint32_t c_nforest, c_loglen, c_nfail, c_nfp, c_rounds, c_complete, c_nlive, c_done;
   __shared__ uint32_t c_ncand;
   const uint32_t V = a.V, W = a.W, tid = threadIdx.x, lane = tid & 31, nt = blockDim.x;
@@ -514,11 +536,12 @@ __global__ void __launch_bounds__(kClThreads, 1) k_recover_cl(RecArgs a) {
         fp++;
       }
     }
-    live = block_sum(live, s_red);
-    nz = block_sum(nz, s_red);
-    fail = block_sum(fail, s_red);
-    fp = block_sum(fp, s_red);
-    const uint32_t ncand = c_ncand;  // final: block_sum synchronised after the last atomicAdd
+    const uint4 sums = block_sum4(make_uint4(live, nz, fail, fp), s_red);
+    live = sums.x;
+    nz = sums.y;
+    fail = sums.z;
+    fp = sums.w;
+    const uint32_t ncand = c_ncand;  // final: block_sum4 synchronised after the last atomicAdd
     if (tid == 0) {
       a.log_live[r] = live;
       a.log_ncand[r] = ncand;
