@@ -399,16 +399,36 @@ __global__ void __launch_bounds__(kRecThreads, 2) k_recover(RecArgs a) {
     CUPC_GRID_SYNC();
     for (uint32_t w = gtid; w < V; w += gstride) a.label[w] = find_root(a.parent, w, V);  // the minimum id
     CUPC_GRID_SYNC();
-    // fragments are the live components of the first round: count members
+    // A fragment that holds no endpoint of a deleted forest edge is a whole
+    // component of the last complete recovery, joined with others only by
+    // recorded merges: its cut is empty, so it starts final (its sample
+    // would be ZERO). Only the split components are sampled again.
+    for (uint32_t w = gtid; w < V; w += gstride)
+      if (ld_cg(&a.label[w]) == w) a.final_[w] = 1;
+    CUPC_GRID_SYNC();
+    for (uint32_t i = gtid; i < nall; i += gstride) {
+      const bool dead = i < nsorted ? a.fdead[i] != 0 : a.fadd_dead[i - nsorted] != 0;
+      if (!dead) continue;
+      const uint64_t e = i < nsorted ? a.forest_sorted[i] : a.fadd[i - nsorted];
+      const uint32_t x = (uint32_t)(e / V), y = (uint32_t)(e % V);
+      if (x < V && y < V) {
+        a.final_[ld_cg(&a.label[x])] = 0;
+        a.final_[ld_cg(&a.label[y])] = 0;
+      }
+    }
+    CUPC_GRID_SYNC();
+    // the split fragments are the live components of the first round: count members
     for (uint32_t base = gwarp * 32; base < V; base += nwarps * 32) {
       const uint32_t w = base + lane;
       uint32_t lab = 0;
+      bool live = false;
       if (w < V) {
         lab = ld_cg(&a.label[w]);
+        live = !ld_cg(&a.final_[lab]);
         a.parent[w] = w;
         a.fdead[w] = 0;
       }
-      const uint32_t m_first = __ballot_sync(0xffffffffu, warp_grab(a.rcnt, lab, w < V) == 0 && w < V);
+      const uint32_t m_first = __ballot_sync(0xffffffffu, warp_grab(a.rcnt, lab, live) == 0 && live);
       if (lane == 0 && m_first) atomicAdd(&gc[GC_NLIVE], (uint32_t)__popc(m_first));
     }
     CUPC_GRID_SYNC();

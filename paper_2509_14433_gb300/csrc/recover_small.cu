@@ -378,12 +378,29 @@ __global__ void __launch_bounds__(kClThreads, 1) k_recover_cl(RecArgs a) {
         if (keep) a.forest[atomicAdd(&c_nforest, 1u)] = e;
       }
       __syncthreads();
+      for (uint32_t w = tid; w < V; w += nt) m.lab[w] = cl_find(m.f, w, V);  // the smallest id of the fragment
+      __syncthreads();
+      // A fragment that holds no endpoint of a deleted forest edge is a whole
+      // component of the last complete recovery, joined with others only by
+      // recorded merges: its cut is empty, so it starts final (its sample
+      // would be ZERO). Only the split components are sampled again.
+      for (uint32_t w = tid; w < V; w += nt) m.fin[w] = m.lab[w] == w;
+      __syncthreads();
+      for (uint32_t i = tid; i < nall; i += nt) {
+        const bool dead = i < nsorted ? a.fdead[i] != 0 : a.fadd_dead[i - nsorted] != 0;
+        if (!dead) continue;
+        const uint64_t e = i < nsorted ? a.forest_sorted[i] : a.fadd[i - nsorted];
+        const uint32_t x = (uint32_t)(e / V), y = (uint32_t)(e % V);
+        if (x < V && y < V) {
+          m.fin[m.lab[x]] = 0;
+          m.fin[m.lab[y]] = 0;
+        }
+      }
+      __syncthreads();
       uint32_t nl = 0;
       for (uint32_t w = tid; w < V; w += nt) {
         a.fdead[w] = 0;
-        const uint32_t root = cl_find(m.f, w, V);  // the smallest id of the fragment
-        m.lab[w] = root;
-        nl += root == w;
+        nl += m.lab[w] == w && !m.fin[w];
       }
       nl = block_sum(nl, s_red);
       if (tid == 0) c_nlive = nl;
