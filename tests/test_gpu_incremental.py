@@ -274,3 +274,43 @@ def test_mixed_batches_keep_the_labels_and_follow_the_order_inside_a_batch():
     assert np.array_equal(dev.query(pairs)[1], ref.query(pairs)[1])
     assert dev.stats()["recoveries"] == rec1
 
+
+
+# V up to 4096 recovers in one thread-block cluster, larger V across the grid
+@pytest.mark.parametrize("V,k", [(600, 20), (5000, 100)])
+def test_warm_start_samples_only_the_split_components(V, k):
+    # k components, each a cycle with chords; deleting one forest edge splits
+    # one component in two: the warm recovery samples those two fragments
+    # only (every other component starts final, its cut being empty) and
+    # finds the replacement edge; answers and labels equal the oracle's
+    from paper_2509_14433_gb300 import cupc as C
+    seed = 81
+    g = WL.rng(seed)
+    s = V // k
+    edges = set()
+    for c in range(k):
+        base = c * s
+        for i in range(s):
+            a, b = base + i, base + (i + 1) % s
+            edges.add((min(a, b), max(a, b)))
+        for _ in range(s // 2):
+            a, b = (base + int(x) for x in g.choice(s, 2, replace=False))
+            edges.add((min(a, b), max(a, b)))
+    E = np.array(sorted(edges), np.uint32)
+    dev, ref = _dev(V, seed), O.Graph(V, seed)
+    assert C.cupc_set_incremental(dev.h, 1, None) == 0
+    assert dev.update(E) == 0 and ref.update(E) == O.OK
+    pairs = WL.uniform_pairs(V, 500, g, distinct=False)
+    assert np.array_equal(dev.query(pairs)[1], ref.query(pairs)[1])
+    st, F = dev.forest()
+    assert st == 0 and len(F) == V - k
+    e = next(int(x) for x in F if (int(x) // V) // s == 3)  # a forest edge of component 3
+    D = np.array([[e // V, e % V]], np.uint32)
+    o = -np.ones(1, np.int8)
+    assert dev.update(D, o) == 0 and ref.update(D, o) == O.OK
+    s1, a1 = dev.query(pairs)
+    s2, a2 = ref.query(pairs)
+    assert s1 == s2 == 0 and np.array_equal(a1, a2)
+    assert dev.round_log()[0][0] == 2  # the two sides of the deleted edge, not all k components
+    assert np.array_equal(dev.labels(), ref.labels())
+    assert len(np.unique(dev.labels())) == k
