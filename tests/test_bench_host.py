@@ -40,3 +40,24 @@ def test_dense_sweep_bytes():
     c = np.full(V, 128)
     ratio = bench.dense_sweep_bytes(c, 16, 197) / (32 * bench.expected_touched_buckets(c, 16, 7, 28))
     assert 3.5 < ratio < 4.0
+
+
+def test_shuffled_parts_is_a_permutation_in_strided_parts(monkeypatch):
+    # streams longer than the device sort's limit are permuted in strided
+    # parts; every element appears exactly once, and each part spans the
+    # whole id range (small limits stand in for 2^31 - 1 and 2^30)
+    torch = __import__("pytest").importorskip("torch")
+    monkeypatch.setattr(bench, "PERM_ONE", 100)
+    monkeypatch.setattr(bench, "PERM_CHUNK", 64)
+    x = torch.arange(1000, dtype=torch.int64) * 7
+    gen = torch.Generator().manual_seed(5)
+    parts = list(bench.shuffled_parts(x, gen))
+    assert len(parts) == 16  # ceil(1000 / 64)
+    y = torch.cat(parts)
+    assert sorted(y.tolist()) == sorted(x.tolist())
+    for p in parts:
+        assert p.min().item() < 7 * 100 and p.max().item() > 7 * 900
+    # at or below the limit: one uniform permutation
+    gen = torch.Generator().manual_seed(5)
+    one = list(bench.shuffled_parts(x[:100], gen))
+    assert len(one) == 1 and sorted(one[0].tolist()) == sorted(x[:100].tolist())
