@@ -283,7 +283,7 @@ __device__ void small_hook(const RecArgs& a, uint32_t n, unsigned char* smem) {
 
 __global__ void __launch_bounds__(kRecThreads, 2) k_recover(RecArgs a) {
   __shared__ int s_ok;
-  __shared__ uint32_t t_w[kRecTile], t_k[kRecTile];
+  __shared__ uint32_t t_w[kRecTile], t_k[kRecTile + 1];
   static_assert(kRecTile <= kRecThreads, "one member id per thread");
   static_assert(sizeof(ulonglong2) * kTileSegs * kRecThreads >= 2 * kSmallHook * (8 + 4 + 4),
                 "small_hook lives in t_stage");
@@ -502,26 +502,27 @@ __global__ void __launch_bounds__(kRecThreads, 2) k_recover(RecArgs a) {
     // vertex per span, every vertex is its own component). A component over
     // several spans is XORed into acc[K]; the last span to finish samples it.
     if (multi) {
-      // big components (more than kRecSpan members): CTA tiles of up to
-      // kRecTile members, thread t XORs bucket t of every member (8 rows in
-      // flight);
-      // each component's part of the tile is staged in shared memory and
-      // sampled by one warp, or XORed into acc[K] when it spans several tiles
-      // (the last tile to finish samples it)
+      // big components (more than kRecSpan members): each CTA takes one
+      // contiguous chunk of their members and walks it in tiles of up to
+      // kRecTile, thread t XORing bucket t of every member (8 rows in
+      // flight). A component's partial sum carries from one tile to the
+      // next, so that a CTA ends each component once: a component inside
+      // one chunk is sampled by one warp, one over several chunks is XORed
+      // into acc[K] once per chunk (the last chunk to finish samples it).
       const uint32_t nbig = ld_cg(&gc[GC_NBIG]);
-      // about one tile per CTA: 16..kRecTile members, a multiple of 8
-      uint32_t tile = (nbig + nb - 1) / nb;
-      tile = min(kRecTile, max(16u, (tile + 7) & ~7u));
-      const uint32_t ntiles = (nbig + tile - 1) / tile;
-      for (uint32_t t = blockIdx.x; t < ntiles; t += nb) {
-        const uint32_t m0 = t * tile, cnt = min(tile, nbig - m0);
+      const uint32_t chunk = max(8u, (((nbig + nb - 1) / nb) + 7) & ~7u);
+      const uint32_t c0 = min(nbig, blockIdx.x * chunk), c1 = min(nbig, c0 + chunk);
+      ulonglong2 acc1 = make_ulonglong2(0, 0);
+      for (uint32_t m0 = c0; m0 < c1; m0 += kRecTile) {
+        const uint32_t cnt = min(kRecTile, c1 - m0);
         if (tid < cnt) {
           const uint32_t w = ld_cg(&a.permb[m0 + tid]);
           t_w[tid] = w;
           t_k[tid] = ld_cg(&a.label[w]);
+        } else if (tid == cnt) {  // the next tile's first label, or none at the chunk's end
+          t_k[cnt] = m0 + cnt < c1 ? ld_cg(&a.label[ld_cg(&a.permb[m0 + cnt])]) : kNoneU32;
         }
         __syncthreads();
-        ulonglong2 acc1 = make_ulonglong2(0, 0);
         uint32_t nseg = 0;
         for (uint32_t m = 0; m < cnt; m += 8) {
           ulonglong2 x[8];
@@ -536,7 +537,7 @@ __global__ void __launch_bounds__(kRecThreads, 2) k_recover(RecArgs a) {
             if (mm < cnt) {
               acc1.x ^= x[k].x;
               acc1.y ^= x[k].y;
-              if (mm + 1 == cnt || t_k[mm + 1] != t_k[mm]) {  // a component's part ends here
+              if (t_k[mm + 1] != t_k[mm]) {  // a component's part of this chunk ends here
                 t_stage[nseg][tid] = acc1;
                 acc1 = make_ulonglong2(0, 0);
                 if (tid == 0) t_seg_k[nseg] = t_k[mm];
@@ -549,7 +550,7 @@ __global__ void __launch_bounds__(kRecThreads, 2) k_recover(RecArgs a) {
         for (uint32_t sg = tid >> 5; sg < nseg; sg += wpb) {
           const uint32_t K = t_seg_k[sg];
           const uint32_t s0 = ld_cg(&a.roff[K]) & ~kBigFlag, s1 = ld_cg(&a.rcnt[K]);
-          const uint32_t ntk = (s1 - 1) / tile - s0 / tile + 1;
+          const uint32_t ntk = (s1 - 1) / chunk - s0 / chunk + 1;  // chunks it meets
           ulonglong2 acc[kWarpBuckets];
 #pragma unroll
           for (uint32_t q = 0; q < kWarpBuckets; q++) acc[q] = t_stage[sg][lane + 32 * q];
